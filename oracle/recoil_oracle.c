@@ -1,0 +1,402 @@
+/*
+ * Recoil oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded restatement of what the Recoil method
+ * computes, used to check the CUDA library path. Only the tests, the smoke
+ * check and the CPU baseline of the benchmark may call it. It shares no code,
+ * header, table or constant with the library, and the library never calls it.
+ *
+ * Every step follows the paper's definitions in the paper's order:
+ *   - rANS coding step ............ Def. 2.1, Eq. 1 (encode) and Eq. 2 (decode)
+ *   - renormalisation ............. Def. 2.2, Eq. 3 (encoder) and Eq. 4 (decoder)
+ *   - W-way interleaving .......... Sec. 2.2 (symbol i is coded by coder i mod W;
+ *                                   within a group, encoders write in increasing
+ *                                   coder order and decoders read in decreasing order)
+ *   - bounded split states ........ Lemma 3.1 (a state taken right after an encoder
+ *                                   renormalisation is below L)
+ *   - split metadata by backward
+ *     scan ....................... Sec. 4.1 (each coder's last renormalisation at or
+ *                                   before the split word)
+ *   - split decoder ............... Sec. 4.1.1-4.1.3 (synchronisation, decoding and
+ *                                   cross-boundary phases)
+ *   - split heuristic ............. Def. 4.1, Eq. 7
+ *   - combining ................... Sec. 3.3 / 4.2 (drop metadata entries)
+ *
+ * Readings where the paper is silent (all listed in the design notes):
+ *   - Quantiser: f[s] = max(1, round_half_even(c[s] 2^n / N)) for present
+ *     symbols, 0 otherwise, then +-1 corrections until the sum is 2^n, visiting
+ *     present symbols cyclically by decreasing initial f (ties: smaller symbol).
+ *   - Indices are 0-based; the recorded index of a split state is the index of
+ *     the last symbol its coder encoded before the renormalisation.
+ *   - An entry is usable only if every coder has such a record with index >= 0.
+ *   - Thread k owns symbols [m_{k-1}, m_k - 1], m = smallest recorded index of
+ *     an entry, m_{-1} = 0, and the final entry owns up to N - 1.
+ *   - Combining keeps entries ceil((k+1) K / M') - 1, k = 0..M'-1.
+ *   - Heuristic ties go to the smaller word offset.
+ *
+ * All arithmetic is integer and exact; states are held in 64-bit integers so
+ * that no intermediate value can wrap.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL -1
+#define OR_ECORRUPT -2
+#define OR_ENOMEM -3
+
+typedef struct {
+    int W;      /* number of interleaved coders */
+    int n;      /* quantisation bits: f and F live on [0, 2^n] */
+    int lgL;    /* renormalisation lower bound L = 2^lgL */
+    int b;      /* bits moved per renormalisation step */
+} oracle_params;
+
+static int params_ok(const oracle_params *P) {
+    if (P->W < 1 || P->W > 64) return 0;
+    if (P->n < 1 || P->n > 16) return 0;
+    if (P->b < P->n || P->b > 16) return 0;         /* one-step renorm needs b >= n (Sec. 4.4) */
+    if (P->lgL < P->n || P->lgL + P->b > 32) return 0; /* L = k 2^n, states below 2^b L <= 2^32 */
+    return 1;
+}
+
+int oracle_params_check(int W, int n, int lgL, int b) {
+    oracle_params P = {W, n, lgL, b};
+    return params_ok(&P) ? OR_OK : OR_EINVAL;
+}
+
+/* ------------------------------------------------------------------ quantiser */
+
+static uint64_t round_half_even_div(uint64_t num, uint64_t den) {
+    uint64_t q = num / den, r = num % den;
+    if (2 * r > den) return q + 1;
+    if (2 * r == den) return q + (q & 1);
+    return q;
+}
+
+/* Quantised PDF f (Def. 2.1) from symbol counts c[0..A). Returns 0 or OR_EINVAL. */
+int oracle_quantize(const uint64_t *c, int A, int n, uint32_t *f) {
+    uint64_t N = 0, total = (uint64_t)1 << n;
+    int present = 0;
+    for (int s = 0; s < A; s++) { N += c[s]; if (c[s]) present++; }
+    if (N == 0 || (uint64_t)present > total) return OR_EINVAL;
+
+    uint64_t sum = 0;
+    for (int s = 0; s < A; s++) {
+        uint64_t v = 0;
+        if (c[s]) {
+            v = round_half_even_div(c[s] << n, N);
+            if (v < 1) v = 1;
+        }
+        f[s] = (uint32_t)v;
+        sum += v;
+    }
+    /* visiting order: present symbols by decreasing f, ties by smaller symbol */
+    int *order = (int *)malloc(sizeof(int) * (size_t)(present ? present : 1));
+    if (!order) return OR_ENOMEM;
+    int m = 0;
+    for (int s = 0; s < A; s++) if (c[s]) order[m++] = s;
+    for (int a = 1; a < m; a++) {            /* insertion sort: stable, obviously correct */
+        int v = order[a], k = a - 1;
+        while (k >= 0 && f[order[k]] < f[v]) { order[k + 1] = order[k]; k--; }
+        order[k + 1] = v;
+    }
+    int pos = 0;
+    while (sum != total) {
+        int s = order[pos];
+        if (sum < total) { f[s] += 1; sum += 1; }
+        else if (f[s] > 1) { f[s] -= 1; sum -= 1; }
+        pos = (pos + 1) % m;
+    }
+    free(order);
+    return OR_OK;
+}
+
+/* F(t) = sum of f below t (the quantised CDF of Def. 2.1), F has A+1 entries. */
+static void cdf_from_pdf(const uint32_t *f, int A, uint64_t *F) {
+    F[0] = 0;
+    for (int s = 0; s < A; s++) F[s + 1] = F[s] + f[s];
+}
+
+/* t such that F(t) <= slot < F(t+1): the last t with F(t) <= slot (Eq. 2). */
+static int find_symbol(const uint64_t *F, int A, uint64_t slot) {
+    int lo = 0, hi = A - 1;                  /* invariant: F[lo] <= slot */
+    while (lo < hi) {
+        int mid = lo + (hi - lo + 1) / 2;
+        if (F[mid] <= slot) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------------------- encoder */
+
+/*
+ * Interleaved rANS encoder (Eqs. 1 and 3, Sec. 2.2).
+ * sym[0..N) are symbols, f the quantised PDF over A symbols.
+ * Writes words B[0..), the final states xf[0..W), and for every word p the
+ * renormalisation event that wrote it: ev_sym[p] = the symbol index whose
+ * coding triggered it (the coder is ev_sym[p] mod W and the recorded index of
+ * the state is ev_sym[p] - W), ev_y[p] = the coder state right after it.
+ * cap is the capacity of B / ev_*. Returns the word count or a negative code.
+ */
+int64_t oracle_encode(const uint32_t *sym, int64_t N, const uint32_t *f, int A,
+                      int W, int n, int lgL, int b,
+                      uint16_t *B, int64_t cap, uint32_t *xf,
+                      int64_t *ev_sym, uint32_t *ev_y) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || N < 0) return OR_EINVAL;
+    uint64_t *F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(A + 1));
+    uint64_t *x = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+    if (!F || !x) { free(F); free(x); return OR_ENOMEM; }
+    cdf_from_pdf(f, A, F);
+    if (F[A] != ((uint64_t)1 << n)) { free(F); free(x); return OR_EINVAL; }
+
+    const uint64_t L = (uint64_t)1 << lgL;
+    const uint64_t wmask = ((uint64_t)1 << b) - 1;
+    for (int j = 0; j < W; j++) x[j] = L;
+    int64_t p = 0;
+    for (int64_t i = 0; i < N; i++) {
+        int j = (int)(i % W);
+        uint32_t s = sym[i];
+        if ((int64_t)s >= A || f[s] == 0) { free(F); free(x); return OR_EINVAL; }
+        uint64_t fs = f[s];
+        /* Eq. 3: the state is renormalised against the f of the symbol about to be coded */
+        while (x[j] >= ((L << b) >> n) * fs) {
+            if (p >= cap) { free(F); free(x); return OR_ENOMEM; }
+            B[p] = (uint16_t)(x[j] & wmask);
+            x[j] >>= b;
+            ev_sym[p] = i;
+            ev_y[p] = (uint32_t)x[j];
+            p++;
+        }
+        /* Eq. 1 */
+        x[j] = ((x[j] / fs) << n) + F[s] + (x[j] % fs);
+    }
+    for (int j = 0; j < W; j++) xf[j] = (uint32_t)x[j];
+    free(F);
+    free(x);
+    return p;
+}
+
+/* -------------------------------------------------------------- serial decode */
+
+/*
+ * Interleaved rANS decoder (Eqs. 2 and 4): from the final states and the last
+ * word backwards to symbol 0. If tr_x / tr_p are non-null, records for every
+ * symbol i the state of its coder right after Eq. 2 (before Eq. 4) and the
+ * word offset p at that moment. end_x[0..W) and *end_p receive the state at
+ * the end (they should be L for every coder and -1).
+ */
+int oracle_decode_serial(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                         const uint32_t *f, int A, int W, int n, int lgL, int b,
+                         uint32_t *out, uint32_t *end_x, int64_t *end_p,
+                         uint32_t *tr_x, int64_t *tr_p) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || N < 0 || nw < 0) return OR_EINVAL;
+    uint64_t *F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(A + 1));
+    uint64_t *x = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+    if (!F || !x) { free(F); free(x); return OR_ENOMEM; }
+    cdf_from_pdf(f, A, F);
+    const uint64_t L = (uint64_t)1 << lgL;
+    const uint64_t mask = ((uint64_t)1 << n) - 1;
+    for (int j = 0; j < W; j++) x[j] = xf[j];
+    int64_t p = nw - 1;
+    int rc = OR_OK;
+    for (int64_t i = N - 1; i >= 0; i--) {
+        int j = (int)(i % W);
+        uint64_t slot = x[j] & mask;
+        int s = find_symbol(F, A, slot);
+        out[i] = (uint32_t)s;
+        x[j] = f[s] * (x[j] >> n) - F[s] + slot;          /* Eq. 2 */
+        if (tr_x) tr_x[i] = (uint32_t)x[j];
+        if (tr_p) tr_p[i] = p;
+        while (x[j] < L) {                                  /* Eq. 4 */
+            if (p < 0) { rc = OR_ECORRUPT; goto done; }
+            x[j] = (x[j] << b) + B[p];
+            p--;
+        }
+    }
+done:
+    if (end_x) for (int j = 0; j < W; j++) end_x[j] = (uint32_t)x[j];
+    if (end_p) *end_p = p;
+    free(F);
+    free(x);
+    return rc;
+}
+
+/* ------------------------------------------------------ split metadata (4.1) */
+
+/*
+ * Backward scan from word q (Sec. 4.1): walk the words q, q-1, ... and take,
+ * for every coder not seen yet, the event that wrote the word. Fills
+ * idx[j] = recorded symbol index (ev_sym - W), y[j] = state, wp[j] = word.
+ * Returns 1 if every coder was found with idx >= 0 (a usable split point),
+ * 0 otherwise.
+ */
+int oracle_scan(const int64_t *ev_sym, const uint32_t *ev_y, int64_t q, int W,
+                int64_t *idx, uint32_t *y, int64_t *wp) {
+    int found = 0;
+    char seen[64];
+    memset(seen, 0, sizeof seen);
+    for (int64_t k = q; k >= 0 && found < W; k--) {
+        int j = (int)(ev_sym[k] % W);
+        if (seen[j]) continue;
+        seen[j] = 1;
+        found++;
+        idx[j] = ev_sym[k] - W;
+        y[j] = ev_y[k];
+        if (wp) wp[j] = k;
+    }
+    if (found < W) return 0;
+    for (int j = 0; j < W; j++) if (idx[j] < 0) return 0;
+    return 1;
+}
+
+static int64_t max_of(const int64_t *v, int W) { int64_t m = v[0]; for (int j = 1; j < W; j++) if (v[j] > m) m = v[j]; return m; }
+static int64_t min_of(const int64_t *v, int W) { int64_t m = v[0]; for (int j = 1; j < W; j++) if (v[j] < m) m = v[j]; return m; }
+static int64_t iabs(int64_t v) { return v < 0 ? -v : v; }
+
+/*
+ * Split heuristic (Def. 4.1, Eq. 7). Chooses up to M-1 split words q[0..) in
+ * increasing order; the final states make the M-th split. For each split,
+ * with lo = the previous split's smallest recorded index (0 for the first),
+ * t = top + 1 - lo and t_s = top + 1 - m, the word minimising
+ * H = |t - T| + |t - t_s - T|, T = ceil(N / M), is taken (ties: smaller word).
+ * The scan for one split stops once m - lo - T exceeds the best H so far,
+ * since m never decreases with the word offset. Returns the number of split
+ * words written to q_out (at most M-1).
+ */
+int64_t oracle_heuristic(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw, int64_t N,
+                         int W, int64_t M, int64_t *q_out) {
+    if (M < 1 || W < 1 || W > 64) return OR_EINVAL;
+    int64_t T = (N + M - 1) / M;
+    int64_t idx[64], wp[64];
+    uint32_t y[64];
+    int64_t count = 0, lo = 0, qprev = -1;
+    while (count < M - 1) {
+        int64_t best = -1, bestH = 0, best_m = 0;
+        for (int64_t q = qprev + 1; q < nw; q++) {
+            if (!oracle_scan(ev_sym, ev_y, q, W, idx, y, wp)) continue;
+            int64_t top = max_of(idx, W), m = min_of(idx, W);
+            if (best >= 0 && m - lo - T > bestH) break;
+            int64_t t = top + 1 - lo, ts = top + 1 - m;
+            int64_t H = iabs(t - T) + iabs(t - ts - T);
+            if (best < 0 || H < bestH) { best = q; bestH = H; best_m = m; }
+        }
+        if (best < 0) break;
+        q_out[count++] = best;
+        lo = best_m;
+        qprev = best;
+    }
+    return count;
+}
+
+/* Combining (Sec. 3.3, 4.2): keep entries ceil((k+1) K / Mp) - 1, k = 0..Mp-1. */
+int64_t oracle_combine(int64_t K, int64_t Mp, int64_t *keep) {
+    if (K < 1 || Mp < 1) return OR_EINVAL;
+    if (Mp > K) Mp = K;
+    for (int64_t k = 0; k < Mp; k++) keep[k] = ((k + 1) * K + Mp - 1) / Mp - 1;
+    return Mp;
+}
+
+/* ----------------------------------------------------- split decoder (4.1.x) */
+
+/* trace codes for one thread's walk */
+#define TR_SKIP 0        /* coder of this symbol not initialised yet */
+#define TR_INIT 1        /* coder initialised from its recorded state */
+#define TR_DECODE 2      /* decoded, discarded (outside the owned range) */
+#define TR_STORE 3       /* decoded and stored */
+
+/*
+ * One split decoder thread (Sec. 4.1.1-4.1.3). If is_final, it starts from the
+ * final states at symbol N-1 with word offset nw-1; otherwise from the entry
+ * (idx[], y[], q): coders start uninitialised at symbol max_j(idx[j]) + W,
+ * coder j takes state y[j] at symbol idx[j] + W and renormalises right away.
+ * It decodes down to symbol lo and stores symbols in [lo, hi].
+ * trace (optional, length >= start+1) receives a TR_* code per visited symbol
+ * and trace_word the word read at that symbol's renormalisation (-1 if none;
+ * the last one read if several). Returns OR_OK or a negative code.
+ */
+int oracle_decode_thread(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                         const uint32_t *f, int A, int W, int n, int lgL, int b,
+                         int is_final, const int64_t *idx, const uint32_t *y, int64_t q,
+                         int64_t lo, int64_t hi, uint32_t *out,
+                         int8_t *trace, int64_t *trace_word) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P)) return OR_EINVAL;
+    uint64_t *F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(A + 1));
+    uint64_t *x = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+    char *init = (char *)malloc((size_t)W);
+    if (!F || !x || !init) { free(F); free(x); free(init); return OR_ENOMEM; }
+    cdf_from_pdf(f, A, F);
+    const uint64_t L = (uint64_t)1 << lgL;
+    const uint64_t mask = ((uint64_t)1 << n) - 1;
+    int64_t p, start;
+    if (is_final) {
+        for (int j = 0; j < W; j++) { x[j] = xf[j]; init[j] = 1; }
+        p = nw - 1;
+        start = N - 1;
+    } else {
+        for (int j = 0; j < W; j++) { x[j] = 0; init[j] = 0; }
+        p = q;
+        start = max_of(idx, W) + W;
+    }
+    int rc = OR_OK;
+    for (int64_t i = start; i >= lo; i--) {
+        int j = (int)(i % W);
+        int8_t code;
+        if (init[j]) {
+            uint64_t slot = x[j] & mask;                     /* Eq. 2 */
+            int s = find_symbol(F, A, slot);
+            x[j] = f[s] * (x[j] >> n) - F[s] + slot;
+            if (i <= hi) { out[i] = (uint32_t)s; code = TR_STORE; } else code = TR_DECODE;
+        } else if (i == idx[j] + W) {
+            x[j] = y[j];                                     /* join at the recorded state */
+            init[j] = 1;
+            code = TR_INIT;
+        } else {
+            if (trace) { trace[i] = TR_SKIP; trace_word[i] = -1; }
+            continue;
+        }
+        int64_t wread = -1;
+        while (x[j] < L) {                                   /* Eq. 4 */
+            if (p < 0) { rc = OR_ECORRUPT; goto done; }
+            x[j] = (x[j] << b) + B[p];
+            wread = p;
+            p--;
+        }
+        if (trace) { trace[i] = code; trace_word[i] = wread; }
+    }
+done:
+    free(F);
+    free(x);
+    free(init);
+    return rc;
+}
+
+/*
+ * Full split decode: K entries, the last being the final states (its idx/y/q
+ * are ignored). idx is K*W (row k = entry k), y is K*W, q is K. Thread k owns
+ * [m_{k-1}, m_k - 1] with m_k = min_j idx[k][j], m_{-1} = 0, and the final
+ * thread owns up to N - 1. The threads run one after another.
+ */
+int oracle_decode_splits(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                         const uint32_t *f, int A, int W, int n, int lgL, int b,
+                         int64_t K, const int64_t *idx, const uint32_t *y, const int64_t *q,
+                         uint32_t *out) {
+    if (K < 1) return OR_EINVAL;
+    int64_t lo = 0;
+    for (int64_t k = 0; k < K; k++) {
+        int is_final = (k == K - 1);
+        int64_t m = is_final ? N : min_of(idx + k * W, W);
+        int64_t hi = m - 1;
+        if (m < lo) return OR_ECORRUPT;
+        int rc = oracle_decode_thread(B, nw, xf, N, f, A, W, n, lgL, b, is_final,
+                                      idx + k * W, y + k * W, is_final ? 0 : q[k],
+                                      lo, hi, out, NULL, NULL);
+        if (rc) return rc;
+        lo = m;
+    }
+    return OR_OK;
+}
