@@ -1,0 +1,325 @@
+"""Benchmark: decoded GB/s of the uneven-stream batch on B300, batched persistent vs per-stream.
+
+Workload (default): 4096 independent streams, lognormal sizes (median 256 KiB,
+sigma 1.5, clipped to 4 KiB .. 64 MiB, about 3.3 GB of symbols), each of
+Laplace(128, b) bytes with its own b ~ U(2, 64) and its own 12-bit table,
+encoded at one split entry per 4096 symbols; all streams decoded in one
+persistent launch from a device work queue (CUDA graph replay). A step is one
+decode of the whole batch. Inputs (3.3 GB out, ~2 GB in) exceed the 126 MB L2.
+
+JSON line keys follow the harness contract; `value` is kernel-side decoded
+GB/s (output symbol bytes / device time), `e2e` the same through the public
+API with the compressed inputs copied from pinned host memory and the decoded
+symbols copied back every step, `per_stream` the one-launch-per-stream
+baseline on the same streams, `roofline` the dominant kernel against the
+measured HBM copy bandwidth, `cpu_baseline` the oracle on host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "decoded GB/s per B300 (batched persistent vs per-stream Recoil); p50/p99 decode latency"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--streams", type=int, default=workloads.BATCH_STREAMS)
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink stream sizes (testing only)")
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--split-symbols", type=int, default=-1)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--per-stream-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+def build_batch(R, count: int, scale: float, rank: int = 0):
+    specs = workloads.batch_specs(count=count, seed=6 + 1000 * rank, scale_sizes=scale)
+    syms = workloads.batch_symbols(specs)
+    threads = max(1, min(64, os.cpu_count() or 1))
+
+    def enc(k):
+        return R.encode_with_splits(syms[k], specs[k].n_bits, workloads.batch_split_count(len(syms[k])))
+
+    with ThreadPoolExecutor(threads) as ex:
+        streams = list(ex.map(enc, range(count)))
+    return specs, syms, streams
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_baseline(specs, syms, seconds: float) -> dict:
+    """The oracle's split decoder, single-threaded, on a bounded sample of the batch."""
+    import oracle
+    order = np.random.default_rng(0).permutation(len(specs))
+    done_syms, busy = 0, 0.0
+    picked = 0
+    for k in order:
+        s = syms[k]
+        o = oracle.encode_with_splits(s, specs[k].n_bits, workloads.batch_split_count(len(s)))
+        t = time.perf_counter()
+        out = oracle.decode_splits(o)
+        busy += time.perf_counter() - t
+        assert np.array_equal(out, s)
+        done_syms += len(s)
+        picked += 1
+        if busy >= seconds:
+            break
+    return {"value": done_syms / busy / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{picked} of {len(specs)} batch streams ({done_syms / 1e6:.1f} MB of symbols), "
+                      f"oracle split decoder (plain C, -O2, one thread), decode time only"}
+
+
+def run_reference(a):
+    """--impl reference: the oracle timed on the host, step = a bounded sample of the batch."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    specs = workloads.batch_specs(count=a.streams, scale_sizes=a.scale)
+    import oracle
+    g = np.random.default_rng(1)
+    budget = max(1.0, 20.0 / max(1, a.steps + a.warmup))
+    times, sizes = [], []
+    for step in range(a.warmup + a.steps):
+        done, t0 = 0, time.perf_counter()
+        busy = 0.0
+        while busy < budget:
+            k = int(g.integers(0, len(specs)))
+            s = specs[k].symbols(threads=1)
+            o = oracle.encode_with_splits(s, specs[k].n_bits, workloads.batch_split_count(len(s)))
+            t = time.perf_counter()
+            oracle.decode_splits(o)
+            busy += time.perf_counter() - t
+            done += len(s)
+        if step >= a.warmup:
+            times.append(busy)
+            sizes.append(done)
+    v = sum(sizes) / sum(times) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": "uneven batch: 4096 Laplace streams, lognormal 4 KiB-64 MiB, n=12",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: random batch streams until {budget:.1f} s of decode"},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    import paper_2306_12141_b300 as R
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    specs, syms, streams = build_batch(R, a.streams, a.scale, rank)
+    out_bytes = sum(len(s) * s.itemsize for s in syms)
+    in_bytes = sum(2 * st.info["n_words"] + 4 * 32 for st in streams)
+
+    split_symbols = 65536 if a.split_symbols < 0 else a.split_symbols
+    opts = {"warps_per_cta": a.warps or 16, "ctas_per_sm": a.ctas_per_sm,
+            "split_symbols": split_symbols, "flags": 4}
+    plan = R.Plan(streams, opts)
+    ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
+    outs = [torch.empty(max(1, len(s) * s.itemsize), dtype=torch.uint8, device=dev) for s in syms]
+    out_ptrs = [o.data_ptr() for o in outs]
+    cs = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            e0.record(cs)
+            fn()
+            e1.record(cs)
+        torch.cuda.synchronize()
+        barrier()
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    with torch.cuda.stream(cs):
+        plan.upload(ws, stream=cs)
+        plan.decode(out_ptrs, cs)
+        assert plan.errors(cs) == 0, R.recoil_last_error()
+        # exactness on the full batch before timing (device compare)
+        bad = 0
+        for s, o in zip(syms, outs):
+            if len(s) and not torch.equal(o[: len(s) * s.itemsize], torch.from_numpy(s.view(np.uint8)).to(dev)):
+                bad += 1
+        assert bad == 0, f"{bad} streams decoded wrong"
+
+        with Clocks(local) as clk:
+            ms = timed(lambda: plan.decode(out_ptrs, cs), a.steps, a.warmup)
+        clocks = clk.summary()
+        launches = plan.launches
+        assert plan.errors(cs) == 0
+
+        # per-stream baseline: one launch per stream, 128-thread blocks, all encoded splits
+        base = R.Plan(streams, {"warps_per_cta": 4, "flags": 1})
+        bws = torch.empty(base.workspace_size, dtype=torch.uint8, device=dev)
+        base.upload(bws, stream=cs)
+        base_ms = timed(lambda: base.decode(out_ptrs, cs), a.per_stream_steps, 1)
+        assert base.errors(cs) == 0
+        base_launches = base.launches
+        del bws
+
+        # end to end through the public API: H2D from pinned host memory, decode, D2H of the symbols
+        e2e = None
+        if not a.no_e2e:
+            for st in streams:
+                R.stream_pin(st)
+            ep = R.Plan(streams, {k: v for k, v in opts.items() if k != "flags"})
+            host_out = torch.empty(out_bytes, dtype=torch.uint8, pin_memory=True)
+            offs = np.concatenate([[0], np.cumsum([max(1, len(s) * s.itemsize) for s in syms])])
+            flat = torch.empty(int(offs[-1]), dtype=torch.uint8, device=dev)
+            flat_ptrs = [flat.data_ptr() + int(o) for o in offs[:-1]]
+            h2d = ep.workspace_size
+
+            def e2e_step():
+                ep.upload(ws, stream=cs)
+                ep.decode(flat_ptrs, cs)
+                host_out.copy_(flat[:out_bytes], non_blocking=True)
+
+            e_ms = timed(e2e_step, max(2, a.steps // 2), 1)
+            e2e = {"value": out_bytes / (statistics.mean(e_ms) * 1e-3) / 1e9, "unit": "GB/s",
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_bytes)}
+            del flat
+
+    mean_ms = statistics.mean(ms)
+    if dist:
+        t = torch.tensor([mean_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    value = world * out_bytes / (mean_ms * 1e-3) / 1e9
+    peaks = measured_peaks()
+    achieved = (out_bytes + in_bytes) / (mean_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"uneven batch: {a.streams} Laplace(128,b~U(2,64)) streams, lognormal sizes "
+                               f"median 256 KiB sigma 1.5 clipped 4 KiB-64 MiB, n=12, W=32, own table each",
+                   "symbols_bytes": out_bytes, "compressed_bytes": in_bytes,
+                   "split_symbols": split_symbols, "warps_per_cta": opts["warps_per_cta"],
+                   "parallelism": f"weak x{world}", "l2": "inputs larger than L2 (no flush)",
+                   "scale": a.scale},
+        "per_stream": {"value": out_bytes / (statistics.mean(base_ms) * 1e-3) / 1e9, "unit": "GB/s",
+                       "ms_per_step": statistics.mean(base_ms), "launches": base_launches,
+                       "speedup": statistics.mean(base_ms) / mean_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peaks["source"], "kernel": "decode_kernel<kPacked8>"},
+        "clocks": clocks,
+        "gpu_launches": launches * a.steps,
+        "e2e": e2e,
+    }
+    if rank == 0 and not a.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(specs, syms, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

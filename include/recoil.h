@@ -1,0 +1,211 @@
+/*
+ * recoil.h -- C-ABI of the B300 Recoil decoder.
+ *
+ * Recoil (Lin et al., "Recoil: Parallel rANS Decoding with Decoder-Adaptive
+ * Scalability", ICPP 2023) encodes data once as ONE 32-way interleaved rANS
+ * bitstream (Sec. 2.2) and records split metadata: for a split word, each
+ * coder's state right after its last renormalisation at or before that word
+ * (bounded by L, Lemma 3.1) and the index of the last symbol it coded
+ * (Sec. 3.1, 4.1). Decoders start at any recorded split, synchronise, decode,
+ * and cross into the previous split's synchronisation section (Sec. 4.1.1-4.1.3).
+ * Splits are combined by dropping metadata entries (Sec. 3.3, 4.2).
+ *
+ * Fixed parameters (Sec. 4.4, Table 3): 32-bit states, 8- or 16-bit symbols,
+ * L = 2^16, 16-bit renormalisation words, n <= 16 quantisation bits, W = 32.
+ *
+ * Conventions
+ *   - Every function returns RECOIL_OK (0) or a negative RECOIL_E* code; the
+ *     message of the last failure on the calling thread is recoil_last_error().
+ *   - Host objects (recoil_stream, recoil_plan) are owned by the library and
+ *     released with recoil_free / recoil_plan_free.
+ *   - Device memory (workspaces, outputs) is owned by the caller: plain device
+ *     pointers, e.g. from torch tensors' data_ptr(). The library never
+ *     allocates device memory.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Decoding is asynchronous on it.
+ *   - Symbols are little-endian uint8 or uint16 arrays of n_syms elements.
+ *   - Nothing here is thread-safe on the same object; distinct objects may be
+ *     used from distinct threads.
+ */
+#ifndef RECOIL_H
+#define RECOIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RECOIL_W 32        /* interleaved coders per stream (Sec. 4.4, Table 3) */
+#define RECOIL_LOG2_L 16   /* renormalisation lower bound L = 2^16 (Table 3) */
+#define RECOIL_B 16        /* bits per renormalisation word b (Table 3) */
+
+#define RECOIL_OK 0
+#define RECOIL_EINVAL (-1)     /* bad argument: null pointer, n outside [1,16], alphabet too large, ... */
+#define RECOIL_ECORRUPT (-2)   /* metadata failed validation, or a kernel found an inconsistent stream */
+#define RECOIL_ENOMEM (-3)     /* host allocation failed, or a caller buffer is too small */
+#define RECOIL_ECUDA (-4)      /* a CUDA runtime call failed (message has the CUDA error) */
+#define RECOIL_ETIMEOUT (-5)   /* a bounded wait expired (serving runtime) */
+
+/* Coding parameters of a stream. n_bits in [1,16] (b = 16 >= n, Sec. 4.4);
+ * sym_bytes 1 (uint8 symbols) or 2 (uint16 symbols). */
+typedef struct {
+  uint32_t n_bits;
+  uint32_t sym_bytes;
+} recoil_params;
+
+typedef struct recoil_stream recoil_stream;   /* opaque host object */
+
+typedef struct {
+  uint64_t n_syms;            /* N */
+  uint64_t n_words;           /* 16-bit words in the bitstream */
+  uint32_t n_entries;         /* split entries, including the final-state entry */
+  uint32_t n_bits;
+  uint32_t sym_bytes;
+  uint32_t alphabet;          /* entries of the frequency table */
+  uint64_t bitstream_bytes;   /* 2 * n_words + 4 * W (final states) */
+  uint64_t metadata_bytes;    /* unpacked split metadata: (8 + 2W + 4W) bytes per regular entry */
+  uint64_t max_sync;          /* largest synchronisation section, in symbols (Sec. 4.1) */
+} recoil_info;
+
+/*
+ * Encode n_syms symbols as one interleaved rANS stream (Eqs. 1 and 3, Sec. 2.2)
+ * and place split entries by the heuristic of Def. 4.1 / Eq. 7.
+ *   syms        host array of n_syms symbols (uint8 or uint16 per params->sym_bytes)
+ *   params      n_bits and sym_bytes
+ *   max_splits  splits M the decoder may use at most, counting the final-state
+ *               entry; the heuristic yields at most M (fewer on short inputs)
+ *   out         receives a new stream (free with recoil_free)
+ * The static quantised PDF comes from the symbol counts (Sec. 5.1): present
+ * symbols get f = max(1, round_half_even(c 2^n / N)), then +-1 corrections
+ * until the sum is 2^n. Errors: RECOIL_EINVAL (null, n outside [1,16],
+ * sym_bytes not 1/2, more distinct symbols than 2^n, n_syms >= 2^31),
+ * RECOIL_ENOMEM. The encoder is serial by design (Sec. 6).
+ */
+int recoil_encode_with_splits(const void* syms, uint64_t n_syms, const recoil_params* params,
+                              uint32_t max_splits, recoil_stream** out);
+
+/*
+ * Combine splits (Sec. 3.3, 4.2): a new stream with min(target_splits, K)
+ * entries, keeping entries ceil((k+1) K / M') - 1 of the K entries of `in`
+ * (the final-state entry always stays). The bitstream is shared, not copied;
+ * `in` is untouched and may be freed independently. O(M' W). Errors: EINVAL.
+ */
+int recoil_combine_splits(const recoil_stream* in, uint32_t target_splits, recoil_stream** out);
+
+/* Sizes and counts of a stream. Errors: EINVAL. */
+int recoil_stream_info(const recoil_stream* s, recoil_info* out);
+
+/*
+ * Copy a stream's parts out (any pointer may be NULL to skip it):
+ *   freq[alphabet], words[n_words], final_states[W],
+ *   entry_word[R], entry_index[R*W] (recorded symbol index per coder),
+ *   entry_state[R*W] (16-bit states), R = n_entries - 1 regular entries.
+ */
+int recoil_stream_export(const recoil_stream* s, uint32_t* freq, uint16_t* words,
+                         uint32_t* final_states, uint64_t* entry_word, uint64_t* entry_index,
+                         uint16_t* entry_state);
+
+/*
+ * Build a stream from parts made elsewhere (e.g. another encoder). Validates
+ * the metadata (Sec. 4.1): frequencies sum to 2^n, words strictly increase,
+ * every recorded index is congruent to its coder modulo W and below n_syms,
+ * states are < L (Lemma 3.1), each entry's smallest index does not decrease,
+ * and the top coder's join lies within the stream. Errors: EINVAL, ECORRUPT.
+ */
+int recoil_stream_import(const recoil_params* params, uint64_t n_syms, uint32_t alphabet,
+                         const uint32_t* freq, const uint16_t* words, uint64_t n_words,
+                         const uint32_t* final_states, uint32_t n_regular,
+                         const uint64_t* entry_word, const uint64_t* entry_index,
+                         const uint16_t* entry_state, recoil_stream** out);
+
+/* Move the stream's words to page-locked host memory (faster host->device
+ * copies). Needs a CUDA driver. Errors: ECUDA. */
+int recoil_stream_pin(recoil_stream* s);
+
+void recoil_free(recoil_stream* s);
+const char* recoil_last_error(void);
+
+/* ------------------------------------------------------------------ device */
+
+/* Batch options. Zero fields take defaults (or the autotuned values). */
+typedef struct {
+  uint32_t warps_per_cta;    /* decoder warps per CTA (4, 8, 16, 32); default 16 */
+  uint32_t ctas_per_sm;      /* persistent CTAs per SM; default: occupancy maximum */
+  uint32_t split_symbols;    /* combine each stream to ceil(N / split_symbols) splits; 0 = keep all */
+  uint32_t flags;            /* RECOIL_BATCH_* */
+} recoil_batch_opts;
+
+#define RECOIL_BATCH_PER_STREAM 1u   /* one launch per stream (paper-style baseline) instead of one persistent launch */
+#define RECOIL_BATCH_NO_SORT 2u      /* keep stream-major item order instead of longest-first */
+#define RECOIL_BATCH_GRAPH 4u        /* capture the launch sequence in a CUDA graph on the first
+                                        recoil_plan_decode and replay it afterwards (needs a
+                                        non-default cuda_stream; ignored with PER_STREAM) */
+
+typedef struct recoil_plan recoil_plan;   /* opaque: device image layout + work queue of a batch */
+
+/*
+ * Plan the decode of `count` streams: combine per opts->split_symbols, lay out
+ * words, tables and entries for the device, and build the CTA work queue
+ * (items of up to warps_per_cta entries of one stream). Host only.
+ * The streams must outlive the plan. Errors: EINVAL, ENOMEM.
+ */
+int recoil_plan_create(const recoil_stream* const* streams, uint32_t count,
+                       const recoil_batch_opts* opts, recoil_plan** out);
+
+/* Device bytes the plan needs (workspace), a multiple of 256. */
+int recoil_plan_workspace_size(const recoil_plan* plan, size_t* bytes);
+
+/*
+ * Copy the plan's device image into d_workspace (>= workspace size bytes,
+ * 256-byte aligned, caller-owned) on cuda_stream. Returns once the copies are
+ * queued; host sources stay valid while the streams and plan live.
+ * Errors: EINVAL (null or too small), ECUDA.
+ */
+int recoil_plan_upload(recoil_plan* plan, void* d_workspace, size_t ws_bytes, void* cuda_stream);
+
+/*
+ * Decode every stream of an uploaded plan: d_outs[i] is a caller-owned device
+ * buffer of n_syms * sym_bytes bytes for stream i. One persistent launch (or
+ * one launch per stream with RECOIL_BATCH_PER_STREAM), asynchronous on
+ * cuda_stream. Kernel-detected inconsistencies are recorded in the workspace
+ * and read with recoil_plan_errors. Errors: EINVAL (not uploaded), ECUDA.
+ */
+int recoil_plan_decode(recoil_plan* plan, void* const* d_outs, void* cuda_stream);
+
+/* Synchronise cuda_stream and read the error flags of the last decode:
+ * *flags = 0 when clean. Returns ECORRUPT if any flag is set. */
+int recoil_plan_errors(recoil_plan* plan, void* cuda_stream, uint32_t* flags);
+
+/* Number of kernel launches the last recoil_plan_decode issued. */
+uint32_t recoil_plan_launches(const recoil_plan* plan);
+
+void recoil_plan_free(recoil_plan* plan);
+
+/* Workspace bytes recoil_decode_batch needs for these streams and options. */
+int recoil_workspace_size(const recoil_stream* const* streams, uint32_t count,
+                          const recoil_batch_opts* opts, size_t* bytes);
+
+/*
+ * Decode one stream into d_out (caller-owned device buffer of
+ * n_syms * sym_bytes bytes): plan, upload into d_workspace, and launch, all
+ * on cuda_stream. Same as recoil_decode_batch with count = 1.
+ */
+int recoil_decode(const recoil_stream* stream, void* d_out, void* d_workspace, size_t ws_bytes,
+                  void* cuda_stream);
+
+/*
+ * Decode many streams of uneven sizes, each with its own table, in one
+ * persistent launch fed by a device work queue (plan + upload + decode).
+ * Errors: as the plan functions.
+ */
+int recoil_decode_batch(const recoil_stream* const* streams, uint32_t count, void* const* d_outs,
+                        void* d_workspace, size_t ws_bytes, void* cuda_stream,
+                        const recoil_batch_opts* opts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECOIL_H */

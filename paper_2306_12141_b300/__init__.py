@@ -1,0 +1,329 @@
+"""Python binding of the B300 Recoil decoder (``librecoil.so``, C-ABI in include/recoil.h).
+
+Argument marshalling only: every step runs in the native library (host
+encoder, combiner, planner) or in its CUDA kernels (decoding). Device memory
+and CUDA streams come from the caller (e.g. torch tensors and
+``torch.cuda.Stream``); pass device pointers as ints or as objects with a
+``data_ptr()`` method and streams as ints or objects with a ``cuda_stream``
+attribute. There is no fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librecoil.so")
+
+W = 32
+OK, EINVAL, ECORRUPT, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
+BATCH_PER_STREAM, BATCH_NO_SORT, BATCH_GRAPH = 1, 2, 4
+
+
+class RecoilError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"recoil error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("n_bits", C.c_uint32), ("sym_bytes", C.c_uint32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_syms", C.c_uint64), ("n_words", C.c_uint64), ("n_entries", C.c_uint32),
+                ("n_bits", C.c_uint32), ("sym_bytes", C.c_uint32), ("alphabet", C.c_uint32),
+                ("bitstream_bytes", C.c_uint64), ("metadata_bytes", C.c_uint64), ("max_sync", C.c_uint64)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_uint32), ("ctas_per_sm", C.c_uint32),
+                ("split_symbols", C.c_uint32), ("flags", C.c_uint32)]
+
+
+EXPORTS = [
+    "recoil_encode_with_splits", "recoil_combine_splits", "recoil_stream_info", "recoil_stream_export",
+    "recoil_stream_import", "recoil_stream_pin", "recoil_free", "recoil_last_error",
+    "recoil_plan_create", "recoil_plan_workspace_size", "recoil_plan_upload", "recoil_plan_decode",
+    "recoil_plan_errors", "recoil_plan_launches", "recoil_plan_free", "recoil_workspace_size",
+    "recoil_decode", "recoil_decode_batch",
+]
+
+_lib = None
+
+
+def lib():
+    """The loaded native library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2306_12141_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+        pp = C.POINTER(C.c_void_p)
+        L.recoil_encode_with_splits.argtypes = [vp, u64, C.POINTER(Params), u32, pp]
+        L.recoil_combine_splits.argtypes = [vp, u32, pp]
+        L.recoil_stream_info.argtypes = [vp, C.POINTER(Info)]
+        L.recoil_stream_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.recoil_stream_import.argtypes = [C.POINTER(Params), u64, u32, vp, vp, u64, vp, u32, vp, vp, vp, pp]
+        L.recoil_stream_pin.argtypes = [vp]
+        L.recoil_free.argtypes = [vp]
+        L.recoil_free.restype = None
+        L.recoil_last_error.restype = C.c_char_p
+        L.recoil_plan_create.argtypes = [vp, u32, C.POINTER(BatchOpts), pp]
+        L.recoil_plan_workspace_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.recoil_plan_upload.argtypes = [vp, vp, C.c_size_t, vp]
+        L.recoil_plan_decode.argtypes = [vp, vp, vp]
+        L.recoil_plan_errors.argtypes = [vp, vp, C.POINTER(u32)]
+        L.recoil_plan_launches.argtypes = [vp]
+        L.recoil_plan_launches.restype = u32
+        L.recoil_plan_free.argtypes = [vp]
+        L.recoil_plan_free.restype = None
+        L.recoil_workspace_size.argtypes = [vp, u32, C.POINTER(BatchOpts), C.POINTER(C.c_size_t)]
+        L.recoil_decode.argtypes = [vp, vp, vp, C.c_size_t, vp]
+        L.recoil_decode_batch.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(BatchOpts)]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise RecoilError(rc, lib().recoil_last_error().decode(errors="replace"))
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream_handle(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _opts(opts) -> BatchOpts | None:
+    if opts is None:
+        return None
+    if isinstance(opts, BatchOpts):
+        return opts
+    return BatchOpts(**opts)
+
+
+# ------------------------------------------------------------------ streams
+class Stream:
+    """A host recoil_stream (owned; freed when garbage collected)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.recoil_free(self.handle)
+            self.handle = None
+
+    @property
+    def info(self) -> dict:
+        return stream_info(self)
+
+    def export(self) -> dict:
+        return stream_export(self)
+
+
+def recoil_encode_with_splits(symbols: np.ndarray, n_bits: int, max_splits: int) -> Stream:
+    s = np.ascontiguousarray(symbols)
+    if s.dtype not in (np.uint8, np.uint16):
+        raise TypeError("symbols must be uint8 or uint16")
+    p = Params(n_bits, s.dtype.itemsize)
+    h = C.c_void_p()
+    _check(lib().recoil_encode_with_splits(s.ctypes.data if s.size else None, s.size, C.byref(p),
+                                           max_splits, C.byref(h)))
+    return Stream(h.value)
+
+
+def recoil_combine_splits(stream: Stream, target_splits: int) -> Stream:
+    h = C.c_void_p()
+    _check(lib().recoil_combine_splits(stream.handle, target_splits, C.byref(h)))
+    return Stream(h.value)
+
+
+def recoil_stream_info(stream: Stream) -> dict:
+    i = Info()
+    _check(lib().recoil_stream_info(stream.handle, C.byref(i)))
+    return {k: getattr(i, k) for k, _ in Info._fields_}
+
+
+def recoil_stream_export(stream: Stream) -> dict:
+    info = recoil_stream_info(stream)
+    R = info["n_entries"] - 1
+    out = {
+        "freq": np.zeros(info["alphabet"], dtype=np.uint32),
+        "words": np.zeros(info["n_words"], dtype=np.uint16),
+        "final": np.zeros(W, dtype=np.uint32),
+        "entry_word": np.zeros(R, dtype=np.uint64),
+        "entry_index": np.zeros((R, W), dtype=np.uint64),
+        "entry_state": np.zeros((R, W), dtype=np.uint16),
+    }
+    _check(lib().recoil_stream_export(stream.handle, *[_ptr(out[k]) if out[k].size else None for k in
+                                                       ("freq", "words", "final", "entry_word",
+                                                        "entry_index", "entry_state")]))
+    return out
+
+
+def recoil_stream_import(n_bits: int, sym_bytes: int, n_syms: int, freq, words, final,
+                         entry_word, entry_index, entry_state) -> Stream:
+    freq = np.ascontiguousarray(freq, dtype=np.uint32)
+    words = np.ascontiguousarray(words, dtype=np.uint16)
+    final = np.ascontiguousarray(final, dtype=np.uint32)
+    ew = np.ascontiguousarray(entry_word, dtype=np.uint64)
+    ei = np.ascontiguousarray(entry_index, dtype=np.uint64)
+    es = np.ascontiguousarray(entry_state, dtype=np.uint16)
+    p = Params(n_bits, sym_bytes)
+    h = C.c_void_p()
+    _check(lib().recoil_stream_import(C.byref(p), n_syms, len(freq), _ptr(freq), _ptr(words) if words.size else None,
+                                      words.size, _ptr(final), len(ew), _ptr(ew) if ew.size else None,
+                                      _ptr(ei) if ei.size else None, _ptr(es) if es.size else None, C.byref(h)))
+    return Stream(h.value)
+
+
+def recoil_stream_pin(stream: Stream) -> None:
+    _check(lib().recoil_stream_pin(stream.handle))
+
+
+# -------------------------------------------------------------------- plans
+def _handles(streams) -> C.Array:
+    arr = (C.c_void_p * max(1, len(streams)))()
+    for k, s in enumerate(streams):
+        arr[k] = s.handle
+    return arr
+
+
+def _ptr_array(ptrs) -> C.Array:
+    arr = (C.c_void_p * max(1, len(ptrs)))()
+    for k, p in enumerate(ptrs):
+        arr[k] = _ptr(p)
+    return arr
+
+
+class Plan:
+    """A recoil_plan: device image layout and work queue of a batch of streams."""
+
+    def __init__(self, streams, opts=None):
+        self.streams = list(streams)          # keep the host streams alive
+        h = C.c_void_p()
+        o = _opts(opts)
+        _check(lib().recoil_plan_create(_handles(self.streams), len(self.streams),
+                                        C.byref(o) if o is not None else None, C.byref(h)))
+        self.handle = h.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.recoil_plan_free(self.handle)
+            self.handle = None
+
+    @property
+    def workspace_size(self) -> int:
+        n = C.c_size_t()
+        _check(lib().recoil_plan_workspace_size(self.handle, C.byref(n)))
+        return n.value
+
+    def upload(self, workspace, nbytes: int | None = None, stream=None) -> None:
+        nb = self.workspace_size if nbytes is None else nbytes
+        _check(lib().recoil_plan_upload(self.handle, _ptr(workspace), nb, _stream_handle(stream)))
+
+    def decode(self, outs, stream=None) -> None:
+        self._outs = _ptr_array(outs)
+        _check(lib().recoil_plan_decode(self.handle, self._outs, _stream_handle(stream)))
+
+    def errors(self, stream=None) -> int:
+        f = C.c_uint32()
+        rc = lib().recoil_plan_errors(self.handle, _stream_handle(stream), C.byref(f))
+        if rc not in (OK, ECORRUPT):
+            _check(rc)
+        return f.value
+
+    @property
+    def launches(self) -> int:
+        return int(lib().recoil_plan_launches(self.handle))
+
+
+def recoil_plan_create(streams, opts=None) -> Plan:
+    return Plan(streams, opts)
+
+
+def recoil_workspace_size(streams, opts=None) -> int:
+    n = C.c_size_t()
+    o = _opts(opts)
+    _check(lib().recoil_workspace_size(_handles(streams), len(streams), C.byref(o) if o is not None else None,
+                                       C.byref(n)))
+    return n.value
+
+
+def recoil_decode(stream: Stream, out, workspace, nbytes: int, cuda_stream=None) -> None:
+    _check(lib().recoil_decode(stream.handle, _ptr(out), _ptr(workspace), nbytes, _stream_handle(cuda_stream)))
+
+
+def recoil_decode_batch(streams, outs, workspace, nbytes: int, cuda_stream=None, opts=None) -> None:
+    o = _opts(opts)
+    _check(lib().recoil_decode_batch(_handles(streams), len(streams), _ptr_array(outs), _ptr(workspace), nbytes,
+                                     _stream_handle(cuda_stream), C.byref(o) if o is not None else None))
+
+
+def recoil_free(stream: Stream) -> None:
+    """Release a stream now instead of at garbage collection."""
+    if stream.handle:
+        lib().recoil_free(stream.handle)
+        stream.handle = None
+
+
+def recoil_last_error() -> str:
+    return lib().recoil_last_error().decode(errors="replace")
+
+
+def recoil_plan_workspace_size(plan: Plan) -> int:
+    return plan.workspace_size
+
+
+def recoil_plan_upload(plan: Plan, workspace, nbytes: int | None = None, cuda_stream=None) -> None:
+    plan.upload(workspace, nbytes, cuda_stream)
+
+
+def recoil_plan_decode(plan: Plan, outs, cuda_stream=None) -> None:
+    plan.decode(outs, cuda_stream)
+
+
+def recoil_plan_errors(plan: Plan, cuda_stream=None) -> int:
+    return plan.errors(cuda_stream)
+
+
+def recoil_plan_launches(plan: Plan) -> int:
+    return plan.launches
+
+
+def recoil_plan_free(plan: Plan) -> None:
+    if plan.handle:
+        lib().recoil_plan_free(plan.handle)
+        plan.handle = None
+
+
+# short aliases
+encode_with_splits = recoil_encode_with_splits
+combine_splits = recoil_combine_splits
+stream_info = recoil_stream_info
+stream_export = recoil_stream_export
+stream_import = recoil_stream_import
+stream_pin = recoil_stream_pin
+workspace_size = recoil_workspace_size
+decode = recoil_decode
+decode_batch = recoil_decode_batch

@@ -1,0 +1,317 @@
+// Recoil split decoders for sm_103a.
+//
+// One warp decodes one split entry; lane j is interleaved coder j (Sec. 2.2,
+// W = 32 matches the warp, Sec. 4.4). Per group step (32 symbols, decreasing
+// index) every lane:
+//   decode   slot = x mod 2^n, table lookup, x = f (x >> n) + slot - F   (Eq. 2)
+//   renorm   coders with x < L read one 16-bit word each (Eq. 4, one step
+//            since b >= n): the warp ballots the need mask, lane j takes the
+//            word p - popc(mask above j) because decoders read in decreasing
+//            coder order (Sec. 2.2), and p drops by popc(mask).
+// A coder joins when the walk reaches one past its recorded symbol (takes the
+// recorded state and renormalises at once, Sec. 4.1.1); groups before every
+// coder has joined are walked with per-lane predicates, the steady middle
+// without. The walk continues into the previous split's synchronisation
+// section and stops at the owned low end (Sec. 4.1.2, 4.1.3).
+//
+// Memory: decoder tables are staged in shared memory once per work item
+// (Sec. 4.4 packs symbol, f and F into one 32-bit entry for 8-bit symbols and
+// n <= 12); the compressed words a warp is about to consume sit in a per-warp
+// shared ring refilled 512 bytes at a time with one 16-byte load per lane,
+// issued a chunk ahead so that the dependent renormalisation reads never wait
+// on HBM. Symbol stores are one coalesced 32-byte (or 64-byte) warp store per
+// group step.
+//
+// Scheduling: persistent CTAs pop work items (up to `warps` entries of one
+// stream) from a device counter; a CTA restages tables only when the stream
+// changes. Every loop is bounded by the entry's group range, every word read
+// comes from the shared ring (in bounds by construction) and every global
+// load of a chunk is guarded by the chunk index, so a corrupt stream yields an
+// error flag, never a fault or a hang.
+#include <cuda_runtime.h>
+
+#include "recoil_internal.h"
+
+namespace recoil {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t lanemask_gt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_gt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------- tables
+
+template <uint32_t KIND>
+struct Tables;
+
+// bias | sym << 12 | f << 20  (bias = slot - F < f < 4096)
+template <>
+struct Tables<kPacked8> {
+  const uint32_t* lut;
+  __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream&) {
+    lut = reinterpret_cast<const uint32_t*>(smem);
+  }
+  __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask) const {
+    const uint32_t e = lut[x & mask];
+    x = (e >> 20) * (x >> n) + (e & 0xfffu);
+    return e >> 12;                        // low byte is the symbol
+  }
+};
+
+// u16 slot -> symbol, then u32 symbol -> (f - 1) << 16 | F
+template <uint32_t KIND>
+struct Tables {
+  const uint16_t* slot_sym;
+  const uint32_t* symtab;
+  __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream& st) {
+    slot_sym = reinterpret_cast<const uint16_t*>(smem);
+    symtab = reinterpret_cast<const uint32_t*>(smem + st.slot_bytes);
+  }
+  __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask) const {
+    const uint32_t slot = x & mask;
+    const uint32_t s = slot_sym[slot];
+    const uint32_t e = symtab[s];
+    x = ((e >> 16) + 1u) * (x >> n) + slot - (e & 0xffffu);
+    return s;
+  }
+};
+
+template <uint32_t KIND>
+struct SymOut {
+  using T = uint8_t;
+};
+template <>
+struct SymOut<kGeneric16> {
+  using T = uint16_t;
+};
+
+// ------------------------------------------------------------- word ring
+// Word w of the stream sits at ring[(w mod 512)] and ring[(w mod 512) + 512];
+// with rp = (p mod 512) + 512, word p - k (0 <= k < 32) is ring[rp - k] for
+// any p, and rp may drift down by up to 128 between normalisations.
+
+__device__ __forceinline__ uint4 load_chunk(const uint16_t* __restrict__ words, int chunk, int lane) {
+  if (chunk < 0) return make_uint4(0, 0, 0, 0);
+  const uint4* src = reinterpret_cast<const uint4*>(words + (size_t)chunk * kChunkWords) + lane;
+  return __ldg(src);
+}
+
+__device__ __forceinline__ void put_chunk(uint16_t* ring, int chunk, int lane, uint4 v) {
+  const int off = (chunk & 1) * kChunkWords + lane * 8;
+  *reinterpret_cast<uint4*>(ring + off) = v;
+  *reinterpret_cast<uint4*>(ring + off + kRingWords) = v;
+}
+
+struct Walker {
+  uint32_t x;          // coder state
+  int p;               // next word to read (stream index), uniform
+  int rp;              // ring position of word p, uniform
+  int cbase;           // first word of the chunk holding p (ring holds cbase-256 .. cbase+255)
+  uint4 pre;           // prefetched chunk (cbase/256 - 2)
+};
+
+template <uint32_t KIND>
+struct EntryDecoder {
+  Tables<KIND> T;
+  const uint16_t* __restrict__ words;
+  uint16_t* ring;
+  typename SymOut<KIND>::T* __restrict__ out;
+  uint32_t n, mask, gt;
+  int lane;
+
+  __device__ __forceinline__ void refill(Walker& w) {
+    __syncwarp();
+    const int cnew = (w.cbase >> 8) - 2;
+    if (cnew >= 0) put_chunk(ring, cnew, lane, w.pre);
+    w.cbase -= kChunkWords;
+    w.pre = load_chunk(words, cnew - 1, lane);
+    __syncwarp();
+  }
+
+  // Eq. 4 for the whole warp: coders with `need` read their word in decreasing coder order.
+  __device__ __forceinline__ void renorm(Walker& w, bool need) {
+    const uint32_t m = __ballot_sync(kFull, need);
+    if (need) {
+      const int k = __popc(m & gt);
+      w.x = (w.x << 16) | ring[w.rp - k];
+    }
+    const int c = __popc(m);
+    w.p -= c;
+    w.rp -= c;
+  }
+
+  // A group step with per-lane predicates (synchronisation phase and range edges).
+  __device__ __forceinline__ void pstep(Walker& w, int g, int act, uint32_t x0, int lo, int hi1) {
+    const int i = g * kW + lane;
+    const bool dec = (g < act) && (i >= lo);
+    const bool join = (g == act);
+    if (dec) {
+      const uint32_t s = T.step(w.x, n, mask);
+      if (i < hi1) out[i] = (typename SymOut<KIND>::T)s;
+    }
+    if (join) w.x = x0;
+    renorm(w, (dec || join) && w.x < kL);
+    w.rp = (w.p & (kRingWords - 1)) + kRingWords;
+    if (w.p < w.cbase) refill(w);
+  }
+
+  // A group step where every coder decodes and every symbol is owned.
+  __device__ __forceinline__ void sstep(Walker& w, typename SymOut<KIND>::T* o) {
+    const uint32_t s = T.step(w.x, n, mask);
+    *o = (typename SymOut<KIND>::T)s;
+    renorm(w, w.x < kL);
+  }
+
+  __device__ void run(const DevEntry* __restrict__ ent, DevControl* ctl, uint32_t entry_id) {
+    const int lo = (int)ent->lo, hi1 = (int)ent->hi1;
+    if (lo >= hi1) return;
+    const uint32_t x0 = ent->x0[lane];
+    const int act = ent->act[lane];
+    int g = ent->g_top;
+
+    Walker w;
+    w.x = 0;
+    w.p = ent->q;
+    w.cbase = (w.p >> 8) << 8;                       // p = -1 gives -256: nothing staged
+    {
+      const int c = w.cbase >> 8;
+      const uint4 a = load_chunk(words, c, lane);
+      const uint4 b = load_chunk(words, c - 1, lane);
+      if (c >= 0) put_chunk(ring, c, lane, a);
+      if (c >= 1) put_chunk(ring, c - 1, lane, b);
+      w.pre = load_chunk(words, c - 2, lane);
+    }
+    __syncwarp();
+    w.rp = (w.p & (kRingWords - 1)) + kRingWords;
+
+    const int g_lo = lo >> 5;
+    const int g_full = __reduce_min_sync(kFull, act);            // below it every coder has joined
+    const int steady_hi = min(g_full - 1, (hi1 >> 5) - 1);       // whole groups owned ...
+    const int steady_lo = (lo + kW - 1) >> 5;                    // ... and fully decodable
+
+    for (; g > steady_hi && g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1);
+
+    if (g >= steady_lo) {
+      typename SymOut<KIND>::T* o = out + (size_t)g * kW + lane;
+      while (g - 3 >= steady_lo) {
+        sstep(w, o);
+        sstep(w, o - kW);
+        sstep(w, o - 2 * kW);
+        sstep(w, o - 3 * kW);
+        o -= 4 * kW;
+        g -= 4;
+        w.rp = (w.p & (kRingWords - 1)) + kRingWords;
+        if (w.p < w.cbase) refill(w);
+      }
+      for (; g >= steady_lo; --g) {
+        sstep(w, o);
+        o -= kW;
+        w.rp = (w.p & (kRingWords - 1)) + kRingWords;
+        if (w.p < w.cbase) refill(w);
+      }
+    }
+
+    for (; g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1);
+
+    // The first thread of a stream must end where the encoder started (Eqs. 1-4 invert).
+    uint32_t err = 0;
+    if (w.p < -1) err |= kErrUnderrun;
+    if (lo == 0 && (w.p != -1 || __any_sync(kFull, w.x != kL))) err |= kErrCorrupt;
+    if (err && lane == 0) {
+      atomicOr(&ctl->errors, err);
+      atomicExch(&ctl->bad_entry, entry_id + 1);
+    }
+  }
+};
+
+template <uint32_t KIND>
+__global__ void __launch_bounds__(1024) decode_kernel(const LaunchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_item;
+  const int warp = threadIdx.x >> 5;
+  uint16_t* ring = reinterpret_cast<uint16_t*>(smem + a.table_smem) + warp * kRingSlots;
+  uint32_t staged = 0xffffffffu;
+  uint32_t it = blockIdx.x;
+  for (;;) {
+    if (a.persistent) {
+      if (threadIdx.x == 0) s_item = atomicAdd(&a.control->head[a.kind], 1u);
+      __syncthreads();
+      it = s_item;
+    }
+    if (it >= a.n_items) break;
+    const DevItem item = a.items[it];
+    const DevStream& st = a.streams[item.stream];
+    if (item.stream != staged) {
+      const uint4* src = reinterpret_cast<const uint4*>(a.table_pool + st.table);
+      uint4* dst = reinterpret_cast<uint4*>(smem);
+      const uint32_t n16 = st.table_bytes >> 4;
+      for (uint32_t k = threadIdx.x; k < n16; k += blockDim.x) dst[k] = __ldg(src + k);
+      staged = item.stream;
+      __syncthreads();
+    }
+    if ((uint32_t)warp < item.count) {
+      EntryDecoder<KIND> d;
+      d.T.bind(smem, st);
+      d.words = a.word_pool + st.words;
+      d.ring = ring;
+      d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[item.stream]);
+      d.n = st.n_bits;
+      d.mask = (1u << st.n_bits) - 1u;
+      d.gt = lanemask_gt();
+      d.lane = threadIdx.x & 31;
+      d.run(a.entries + item.entry + warp, a.control, item.entry + warp);
+    }
+    if (!a.persistent) break;
+    __syncthreads();
+  }
+}
+
+template <uint32_t KIND>
+size_t smem_bytes(uint32_t warps, uint32_t table_smem) {
+  return (size_t)table_smem + (size_t)warps * kRingSlots * sizeof(uint16_t);
+}
+
+template <uint32_t KIND>
+cudaError_t launch_kind(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  const size_t sm = smem_bytes<KIND>(a.warps, a.table_smem);
+  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  decode_kernel<KIND><<<grid, a.warps * 32, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <uint32_t KIND>
+int occupancy_kind(uint32_t warps, uint32_t table_smem, int* out) {
+  const size_t sm = smem_bytes<KIND>(warps, table_smem);
+  if (cudaFuncSetAttribute(decode_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return -1;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND>, (int)warps * 32, sm) == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  switch (kind) {
+    case kPacked8: return launch_kind<kPacked8>(a, grid, s);
+    case kGeneric8: return launch_kind<kGeneric8>(a, grid, s);
+    case kGeneric16: return launch_kind<kGeneric16>(a, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out) {
+  switch (kind) {
+    case kPacked8: return occupancy_kind<kPacked8>(warps, table_smem, out);
+    case kGeneric8: return occupancy_kind<kGeneric8>(warps, table_smem, out);
+    case kGeneric16: return occupancy_kind<kGeneric16>(warps, table_smem, out);
+  }
+  return -1;
+}
+
+size_t ring_smem_per_warp() { return (size_t)kRingSlots * sizeof(uint16_t); }
+
+}  // namespace recoil

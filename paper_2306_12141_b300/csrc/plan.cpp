@@ -1,0 +1,446 @@
+// Decode plans: the device image of a batch of streams (words, decoder
+// tables, one descriptor per kept split entry) and the CTA work queue, plus
+// upload and launch. A single stream is a batch of one.
+//
+// Workspace layout (caller-owned device memory, every segment 256-B aligned):
+//   control | output pointers | stream descriptors | work items | entries |
+//   decoder tables | words (each stream's words start on a 512-B chunk)
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "recoil_internal.h"
+
+namespace recoil {
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint32_t kMaxSmem = 227 * 1024;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+uint32_t table_kind_of(const Stream& s) {
+  if (s.sym_bytes == 2) return kGeneric16;
+  if (s.n_bits <= 12 && !s.constant()) return kPacked8;
+  return kGeneric8;
+}
+
+// Decoder tables of a stream (built once and cached on the stream).
+const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_t* slot_bytes) {
+  std::lock_guard<std::mutex> g(s.cache_mu);
+  const uint32_t n = s.n_bits, slots = 1u << n, A = s.alphabet();
+  const uint32_t k = table_kind_of(s);
+  const uint32_t sb = (uint32_t)align_up((size_t)slots * 2, 16);
+  if (s.table_img.empty()) {
+    if (k == kPacked8) {
+      s.table_img.assign(align_up((size_t)slots * 4, 16), 0);
+      uint32_t* lut = reinterpret_cast<uint32_t*>(s.table_img.data());
+      uint32_t F = 0;
+      for (uint32_t sym = 0; sym < A; sym++) {
+        const uint32_t f = s.freq[sym];
+        for (uint32_t b = 0; b < f; b++) lut[F + b] = b | (sym << 12) | (f << 20);
+        F += f;
+      }
+    } else {
+      s.table_img.assign(sb + align_up((size_t)A * 4, 16), 0);
+      uint16_t* slot_sym = reinterpret_cast<uint16_t*>(s.table_img.data());
+      uint32_t* symtab = reinterpret_cast<uint32_t*>(s.table_img.data() + sb);
+      uint32_t F = 0;
+      for (uint32_t sym = 0; sym < A; sym++) {
+        const uint32_t f = s.freq[sym];
+        for (uint32_t b = 0; b < f; b++) slot_sym[F + b] = (uint16_t)sym;
+        symtab[sym] = f ? (((f - 1) << 16) | F) : 0;
+        F += f;
+      }
+    }
+    s.table_kind = k;
+  }
+  *kind = s.table_kind;
+  *slot_bytes = k == kPacked8 ? 0 : sb;
+  return s.table_img;
+}
+
+// Device entries of a stream: kept regular entries in order, then the final one.
+void build_entries(const Stream& s, std::vector<DevEntry>& out) {
+  const uint32_t N = (uint32_t)s.n_syms;
+  uint32_t prev_m = 0;
+  for (const Entry& e : s.entries) {
+    DevEntry d;
+    uint32_t mn = e.idx[0], mx = e.idx[0];
+    for (int j = 0; j < kW; j++) {
+      d.x0[j] = e.y[j];
+      d.act[j] = (int32_t)(e.idx[j] / kW) + 1;      // joins one group above its recorded symbol
+      mn = std::min(mn, e.idx[j]);
+      mx = std::max(mx, e.idx[j]);
+    }
+    d.q = (int32_t)e.word;
+    d.g_top = (int32_t)(mx / kW) + 1;
+    d.lo = prev_m;
+    d.hi1 = mn;                                      // owns [previous m, m - 1] (Sec. 4.1.3)
+    prev_m = mn;
+    out.push_back(d);
+  }
+  DevEntry d;
+  int32_t top = 0;
+  for (int j = 0; j < kW; j++) {
+    d.x0[j] = s.final_x[j];
+    if ((uint32_t)j < N) {
+      const uint32_t last = (uint32_t)j + kW * ((N - 1 - (uint32_t)j) / kW);
+      d.act[j] = (int32_t)(last / kW) + 1;
+    } else {
+      d.act[j] = 0;                                  // coder never coded a symbol
+    }
+    top = std::max(top, d.act[j]);
+  }
+  d.q = (int32_t)s.n_words() - 1;
+  d.g_top = top;
+  d.lo = prev_m;
+  d.hi1 = N;
+  out.push_back(d);
+}
+
+}  // namespace
+}  // namespace recoil
+
+using namespace recoil;
+
+struct recoil_plan {
+  std::vector<std::unique_ptr<recoil_stream>> owned;   // combined copies
+  std::vector<const Stream*> streams;
+  recoil_batch_opts opts{};
+  uint32_t warps = 16;
+
+  std::vector<uint8_t> meta;                           // control .. entries
+  std::vector<uint8_t> tables;
+  size_t off_outs = 0, off_streams = 0, off_items = 0, off_entries = 0;
+  size_t off_tables = 0, off_words = 0, ws_bytes = 0;
+  std::vector<uint64_t> word_off;                      // per stream, in words
+  uint32_t n_items = 0;
+  uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {};
+  std::vector<uint32_t> stream_kind, stream_item_first, stream_item_count;
+
+  uint8_t* d_ws = nullptr;
+  bool uploaded = false;
+  std::vector<void*> outs;
+  bool outs_on_device = false;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  uint32_t launches = 0;
+  int sms = 0;
+
+  ~recoil_plan() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+static int plan_build(recoil_plan* P) {
+  const uint32_t count = (uint32_t)P->streams.size();
+  const uint32_t warps = P->warps;
+  std::vector<DevStream> ds(count);
+  std::vector<DevEntry> entries;
+  struct ItemK { DevItem it; uint32_t kind; };
+  std::vector<ItemK> items;
+  size_t table_off = 0;
+  uint64_t word_off = 0;
+  P->word_off.resize(count);
+  P->stream_kind.resize(count);
+  std::vector<std::pair<size_t, const std::vector<uint8_t>*>> tabs;
+  for (uint32_t i = 0; i < count; i++) {
+    const Stream& s = *P->streams[i];
+    uint32_t kind = 0, slot_bytes = 0;
+    const std::vector<uint8_t>& img = table_image(s, &kind, &slot_bytes);
+    DevStream& d = ds[i];
+    std::memset(&d, 0, sizeof d);
+    d.words = word_off;
+    d.table = table_off;
+    d.n_words = (uint32_t)s.n_words();
+    d.n_bits = s.n_bits;
+    d.kind = kind;
+    d.alphabet = s.alphabet();
+    d.sym_bytes = s.sym_bytes;
+    d.table_bytes = (uint32_t)img.size();
+    d.slot_bytes = slot_bytes;
+    P->word_off[i] = word_off;
+    P->stream_kind[i] = kind;
+    tabs.push_back({table_off, &img});
+    table_off += img.size();
+    word_off += align_up(s.n_words(), kChunkWords);
+    P->kind_smem[kind] = std::max<uint32_t>(P->kind_smem[kind], d.table_bytes);
+
+    const size_t first = entries.size();
+    build_entries(s, entries);
+    for (size_t e = first; e < entries.size(); e += warps) {
+      ItemK ik;
+      ik.it.stream = i;
+      ik.it.entry = (uint32_t)e;
+      ik.it.count = (uint32_t)std::min<size_t>(warps, entries.size() - e);
+      uint32_t work = 0;
+      for (uint32_t k = 0; k < ik.it.count; k++) {
+        const DevEntry& de = entries[e + k];
+        const int64_t span = (int64_t)de.g_top * kW - (int64_t)de.lo;
+        work = std::max<uint32_t>(work, (uint32_t)std::max<int64_t>(0, std::min<int64_t>(span, 0x7fffffff)));
+      }
+      ik.it.work = work;
+      ik.kind = kind;
+      items.push_back(ik);
+    }
+  }
+  for (uint32_t k = 0; k < kKinds; k++) {
+    if (P->kind_smem[k] + warps * ring_smem_per_warp() > kMaxSmem)
+      return fail(RECOIL_EINVAL, "decoder tables too large for shared memory (alphabet or n too large)");
+  }
+  // item order: by kind; persistent mode longest first, per-stream mode by stream
+  const bool per_stream = P->opts.flags & RECOIL_BATCH_PER_STREAM;
+  const bool sort = !per_stream && !(P->opts.flags & RECOIL_BATCH_NO_SORT);
+  std::stable_sort(items.begin(), items.end(), [&](const ItemK& a, const ItemK& b) {
+    if (per_stream) return a.it.stream < b.it.stream;
+    if (a.kind != b.kind) return a.kind < b.kind;
+    return sort ? a.it.work > b.it.work : false;
+  });
+  P->n_items = (uint32_t)items.size();
+  P->stream_item_first.assign(count, 0);
+  P->stream_item_count.assign(count, 0);
+  for (uint32_t k = 0; k < kKinds; k++) P->kind_count[k] = 0;
+  for (uint32_t x = 0; x < P->n_items; x++) {
+    const uint32_t k = items[x].kind, s = items[x].it.stream;
+    if (P->kind_count[k] == 0) P->kind_first[k] = x;
+    P->kind_count[k]++;
+    if (P->stream_item_count[s] == 0) P->stream_item_first[s] = x;
+    P->stream_item_count[s]++;
+  }
+
+  P->off_outs = sizeof(DevControl);
+  P->off_streams = P->off_outs + align_up((size_t)count * 8, kAlign);
+  P->off_items = P->off_streams + align_up((size_t)count * sizeof(DevStream), kAlign);
+  P->off_entries = P->off_items + align_up(items.size() * sizeof(DevItem), kAlign);
+  const size_t meta_bytes = P->off_entries + align_up(entries.size() * sizeof(DevEntry), kAlign);
+  P->off_tables = meta_bytes;
+  P->off_words = P->off_tables + align_up(table_off, kAlign);
+  P->ws_bytes = P->off_words + align_up((size_t)(word_off + kChunkWords) * 2, kAlign);
+
+  P->meta.assign(meta_bytes, 0);
+  std::memcpy(P->meta.data() + P->off_streams, ds.data(), ds.size() * sizeof(DevStream));
+  DevItem* it = reinterpret_cast<DevItem*>(P->meta.data() + P->off_items);
+  for (size_t x = 0; x < items.size(); x++) it[x] = items[x].it;
+  std::memcpy(P->meta.data() + P->off_entries, entries.data(), entries.size() * sizeof(DevEntry));
+  P->tables.assign(align_up(table_off, 16), 0);
+  for (auto& t : tabs) std::memcpy(P->tables.data() + t.first, t.second->data(), t.second->size());
+  return RECOIL_OK;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(RECOIL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static int plan_launch(recoil_plan* P, cudaStream_t cs) {
+  P->launches = 0;
+  DevControl* ctl = reinterpret_cast<DevControl*>(P->d_ws);
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DevControl), cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  LaunchArgs a{};
+  a.streams = reinterpret_cast<const DevStream*>(P->d_ws + P->off_streams);
+  a.entries = reinterpret_cast<const DevEntry*>(P->d_ws + P->off_entries);
+  a.word_pool = reinterpret_cast<const uint16_t*>(P->d_ws + P->off_words);
+  a.table_pool = P->d_ws + P->off_tables;
+  a.outs = reinterpret_cast<void* const*>(P->d_ws + P->off_outs);
+  a.control = ctl;
+  a.warps = P->warps;
+  const DevItem* items = reinterpret_cast<const DevItem*>(P->d_ws + P->off_items);
+  if (P->opts.flags & RECOIL_BATCH_PER_STREAM) {
+    for (size_t s = 0; s < P->streams.size(); s++) {
+      if (!P->stream_item_count[s]) continue;
+      const uint32_t k = P->stream_kind[s];
+      a.items = items + P->stream_item_first[s];
+      a.n_items = P->stream_item_count[s];
+      a.kind = k;
+      a.persistent = 0;
+      a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
+      e = launch_decode(k, a, a.n_items, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+      P->launches++;
+    }
+    return RECOIL_OK;
+  }
+  for (uint32_t k = 0; k < kKinds; k++) {
+    if (!P->kind_count[k]) continue;
+    a.items = items + P->kind_first[k];
+    a.n_items = P->kind_count[k];
+    a.kind = k;
+    a.persistent = 1;
+    a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
+    int per_sm = (int)P->opts.ctas_per_sm;
+    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, a.table_smem, &per_sm) != 0)
+      return fail(RECOIL_ECUDA, "occupancy query failed");
+    if (per_sm <= 0) return fail(RECOIL_EINVAL, "kernel does not fit on an SM with these options");
+    const unsigned grid = (unsigned)std::min<uint64_t>(a.n_items, (uint64_t)per_sm * P->sms);
+    e = launch_decode(k, a, grid, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    P->launches++;
+  }
+  return RECOIL_OK;
+}
+
+extern "C" {
+
+int recoil_plan_create(const recoil_stream* const* streams, uint32_t count, const recoil_batch_opts* opts,
+                       recoil_plan** out) {
+  clear_error();
+  if (!out || (count && !streams)) return fail(RECOIL_EINVAL, "null argument");
+  *out = nullptr;
+  try {
+    std::unique_ptr<recoil_plan> P(new recoil_plan());
+    if (opts) P->opts = *opts;
+    P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta : 16;
+    if (P->warps < 1 || P->warps > 32) return fail(RECOIL_EINVAL, "warps_per_cta must be in [1, 32]");
+    for (uint32_t i = 0; i < count; i++) {
+      if (!streams[i]) return fail(RECOIL_EINVAL, "null stream");
+      const recoil_stream* s = streams[i];
+      if (P->opts.split_symbols) {
+        const uint64_t want = std::max<uint64_t>(1, (s->n_syms + P->opts.split_symbols - 1) / P->opts.split_symbols);
+        recoil_stream* c = nullptr;
+        int rc = recoil_combine_splits(s, (uint32_t)std::min<uint64_t>(want, 0xffffffffu), &c);
+        if (rc) return rc;
+        P->owned.emplace_back(c);
+        P->streams.push_back(c);
+      } else {
+        P->streams.push_back(s);
+      }
+    }
+    int rc = plan_build(P.get());
+    if (rc) return rc;
+    *out = P.release();
+    return RECOIL_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(RECOIL_ENOMEM, "host allocation failed");
+  }
+}
+
+int recoil_plan_workspace_size(const recoil_plan* P, size_t* bytes) {
+  clear_error();
+  if (!P || !bytes) return fail(RECOIL_EINVAL, "null argument");
+  *bytes = P->ws_bytes;
+  return RECOIL_OK;
+}
+
+int recoil_plan_upload(recoil_plan* P, void* d_ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!P || !d_ws) return fail(RECOIL_EINVAL, "null argument");
+  if (ws_bytes < P->ws_bytes) return fail(RECOIL_ENOMEM, "workspace too small");
+  if (((uintptr_t)d_ws) % kAlign) return fail(RECOIL_EINVAL, "workspace must be 256-byte aligned");
+  cudaStream_t cs = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)d_ws;
+  if (P->sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+  }
+  cudaError_t e = cudaMemcpyAsync(ws, P->meta.data(), P->meta.size(), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && !P->tables.empty())
+    e = cudaMemcpyAsync(ws + P->off_tables, P->tables.data(), P->tables.size(), cudaMemcpyHostToDevice, cs);
+  for (size_t i = 0; e == cudaSuccess && i < P->streams.size(); i++) {
+    const Stream& s = *P->streams[i];
+    if (!s.n_words()) continue;
+    e = cudaMemcpyAsync(ws + P->off_words + P->word_off[i] * 2, s.word_data(), s.n_words() * 2,
+                        cudaMemcpyHostToDevice, cs);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "upload");
+  if (P->d_ws != ws && P->graph) {
+    cudaGraphExecDestroy(P->graph);
+    P->graph = nullptr;
+  }
+  P->d_ws = ws;
+  P->uploaded = true;
+  P->outs_on_device = false;
+  return RECOIL_OK;
+}
+
+int recoil_plan_decode(recoil_plan* P, void* const* d_outs, void* stream) {
+  clear_error();
+  if (!P || (!d_outs && !P->streams.empty())) return fail(RECOIL_EINVAL, "null argument");
+  if (!P->uploaded) return fail(RECOIL_EINVAL, "plan not uploaded");
+  cudaStream_t cs = (cudaStream_t)stream;
+  const size_t count = P->streams.size();
+  bool same = P->outs_on_device && P->outs.size() == count;
+  for (size_t i = 0; same && i < count; i++) same = P->outs[i] == d_outs[i];
+  if (!same) {
+    for (size_t i = 0; i < count; i++)
+      if (!d_outs[i] && P->streams[i]->n_syms) return fail(RECOIL_EINVAL, "null output buffer");
+    P->outs.assign(d_outs, d_outs + count);
+    cudaError_t e = cudaMemcpyAsync(P->d_ws + P->off_outs, P->outs.data(), count * 8, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "output pointer upload");
+    P->outs_on_device = true;
+  }
+  const bool use_graph = (P->opts.flags & RECOIL_BATCH_GRAPH) && cs != nullptr &&
+                         !(P->opts.flags & RECOIL_BATCH_PER_STREAM);
+  if (!use_graph) return plan_launch(P, cs);
+  if (!P->graph) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    int rc = plan_launch(P, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&P->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  cudaError_t e = cudaGraphLaunch(P->graph, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return RECOIL_OK;
+}
+
+int recoil_plan_errors(recoil_plan* P, void* stream, uint32_t* flags) {
+  clear_error();
+  if (!P || !flags) return fail(RECOIL_EINVAL, "null argument");
+  if (!P->uploaded) return fail(RECOIL_EINVAL, "plan not uploaded");
+  DevControl c;
+  cudaError_t e = cudaMemcpyAsync(&c, P->d_ws, sizeof c, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "error readback");
+  *flags = c.errors;
+  if (c.errors)
+    return fail(RECOIL_ECORRUPT, "decoder found an inconsistent stream (flags " + std::to_string(c.errors) +
+                                     ", entry " + std::to_string((long long)c.bad_entry - 1) + ")");
+  return RECOIL_OK;
+}
+
+uint32_t recoil_plan_launches(const recoil_plan* P) { return P ? P->launches : 0; }
+
+void recoil_plan_free(recoil_plan* P) { delete P; }
+
+int recoil_workspace_size(const recoil_stream* const* streams, uint32_t count, const recoil_batch_opts* opts,
+                          size_t* bytes) {
+  recoil_plan* P = nullptr;
+  int rc = recoil_plan_create(streams, count, opts, &P);
+  if (rc) return rc;
+  rc = recoil_plan_workspace_size(P, bytes);
+  recoil_plan_free(P);
+  return rc;
+}
+
+int recoil_decode_batch(const recoil_stream* const* streams, uint32_t count, void* const* d_outs, void* d_ws,
+                        size_t ws_bytes, void* stream, const recoil_batch_opts* opts) {
+  recoil_plan* P = nullptr;
+  int rc = recoil_plan_create(streams, count, opts, &P);
+  if (rc) return rc;
+  recoil_batch_opts o = P->opts;
+  o.flags &= ~RECOIL_BATCH_GRAPH;                 // a one-shot plan has nothing to replay
+  P->opts = o;
+  rc = recoil_plan_upload(P, d_ws, ws_bytes, stream);
+  if (!rc) rc = recoil_plan_decode(P, d_outs, stream);
+  recoil_plan_free(P);
+  return rc;
+}
+
+int recoil_decode(const recoil_stream* s, void* d_out, void* d_ws, size_t ws_bytes, void* stream) {
+  const recoil_stream* ss[1] = {s};
+  void* outs[1] = {d_out};
+  return recoil_decode_batch(ss, 1, outs, d_ws, ws_bytes, stream, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal types of the Recoil library: the host stream object and the
+// device-side descriptors the decode kernels read. Not part of the C-ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "recoil.h"
+
+namespace recoil {
+
+constexpr int kW = RECOIL_W;                 // interleaved coders = warp width
+constexpr int kLgL = RECOIL_LOG2_L;          // L = 2^16
+constexpr uint32_t kL = 1u << kLgL;
+constexpr int kB = RECOIL_B;                 // 16-bit renormalisation words
+constexpr int kChunkWords = 256;             // words per refill of a warp's ring (512 B)
+constexpr int kRingWords = 512;              // words a warp keeps staged (two chunks)
+constexpr int kRingSlots = 2 * kRingWords;   // each staged word is stored twice (wrap-free reads)
+
+// Decoder table kinds.
+enum TableKind : uint32_t {
+  kPacked8 = 0,    // 8-bit symbols, n <= 12, f < 4096: one u32 per slot = bias | sym << 12 | f << 20
+  kGeneric8 = 1,   // 8-bit symbols otherwise: u16 slot -> symbol, u32 symbol -> (f-1) << 16 | F
+  kGeneric16 = 2,  // 16-bit symbols: same tables as kGeneric8, 16-bit stores
+  kKinds = 3,
+};
+
+// One split entry as kept on the host (Sec. 4.1 metadata, unpacked).
+struct Entry {
+  uint64_t word;             // split word q: the decoder's first read
+  uint32_t idx[kW];          // recorded symbol index per coder (last symbol coded before the renorm)
+  uint16_t y[kW];            // state right after that renormalisation (< L by Lemma 3.1)
+};
+
+// Host stream: everything the encoder produced. Words are shared between a
+// stream and the streams combined from it, so combining copies no bitstream.
+struct Stream {
+  uint32_t n_bits = 0;
+  uint32_t sym_bytes = 1;
+  uint64_t n_syms = 0;
+  std::vector<uint32_t> freq;                      // quantised PDF f over the alphabet
+  std::shared_ptr<const std::vector<uint16_t>> words;
+  const uint16_t* pinned_words = nullptr;          // optional page-locked copy of the words
+  uint32_t final_x[kW] = {};
+  std::vector<Entry> entries;                      // regular entries, increasing word; final is implicit
+
+  // caches of the device-side images (built on first use)
+  mutable std::mutex cache_mu;
+  mutable std::vector<uint8_t> table_img;          // decoder tables, padded to 16 B
+  mutable uint32_t table_kind = 0;
+
+  ~Stream();
+  uint64_t n_words() const { return words ? words->size() : 0; }
+  const uint16_t* word_data() const { return pinned_words ? pinned_words : (words ? words->data() : nullptr); }
+  uint32_t alphabet() const { return (uint32_t)freq.size(); }
+  bool constant() const;                           // a single symbol owns all 2^n slots
+};
+
+// ------------------------------------------------------------ device images
+
+// One decoder thread (one warp): a kept entry with its owned range.
+struct alignas(16) DevEntry {
+  int32_t q;                 // first word read (-1: the stream has no words)
+  int32_t g_top;             // first group visited
+  uint32_t lo;               // first owned symbol
+  uint32_t hi1;              // one past the last owned symbol (lo == hi1: nothing owned)
+  uint32_t x0[kW];           // state a coder takes when it joins
+  int32_t act[kW];           // group at which a coder joins (takes x0, renormalises)
+};
+static_assert(sizeof(DevEntry) == 16 + 8 * kW, "DevEntry layout");
+
+struct alignas(16) DevStream {
+  uint64_t words;            // element offset of the stream's words in the word pool (multiple of 256)
+  uint64_t table;            // byte offset of the stream's tables in the table pool (multiple of 16)
+  uint32_t n_words;
+  uint32_t n_bits;
+  uint32_t kind;             // TableKind
+  uint32_t alphabet;
+  uint32_t sym_bytes;
+  uint32_t table_bytes;      // bytes of the table image (multiple of 16)
+  uint32_t slot_bytes;       // generic kind: bytes of the slot -> symbol part (multiple of 16)
+  uint32_t pad;
+};
+static_assert(sizeof(DevStream) == 48, "DevStream layout");
+
+// A unit of work for one CTA: up to warps_per_cta consecutive entries of one stream.
+struct alignas(16) DevItem {
+  uint32_t stream;
+  uint32_t entry;            // first DevEntry
+  uint32_t count;            // number of entries (<= warps per CTA)
+  uint32_t work;             // estimated symbols decoded (for ordering)
+};
+
+struct alignas(16) DevControl {
+  uint32_t head[4];          // persistent queue position, one per table kind
+  uint32_t errors;           // kErr* bits
+  uint32_t bad_entry;        // an entry that raised an error (+1), 0 if none
+  uint32_t pad[58];
+};
+static_assert(sizeof(DevControl) == 256, "DevControl layout");
+
+// Error flags raised by kernels.
+constexpr uint32_t kErrCorrupt = 1u;         // first thread did not end at p = -1 with all states = L
+constexpr uint32_t kErrUnderrun = 2u;        // a read went below word 0
+
+// Arguments of one kernel launch.
+struct LaunchArgs {
+  const DevItem* items;      // items of this launch (one table kind)
+  uint32_t n_items;
+  uint32_t kind;
+  uint32_t persistent;       // 1: CTAs pop items from control->head; 0: one item per CTA
+  const DevStream* streams;
+  const DevEntry* entries;
+  const uint16_t* word_pool;
+  const uint8_t* table_pool;
+  void* const* outs;         // device array: output pointer per stream
+  DevControl* control;
+  uint32_t table_smem;       // bytes reserved for tables in shared memory
+  uint32_t warps;            // warps per CTA
+};
+
+// Kernel launchers (decode_kernels.cu).
+cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s);
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out);
+size_t ring_smem_per_warp();
+
+// Error reporting (thread-local message).
+int fail(int code, const std::string& msg);
+void clear_error();
+
+}  // namespace recoil
+
+struct recoil_stream : recoil::Stream {};

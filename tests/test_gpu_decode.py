@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA split decoders against the oracle, bit for bit.
+
+All decoding goes through the C-ABI (plan, upload, decode). Expected values
+are the input symbols (the codec is lossless) and the oracle's own split
+decode of the same stream; streams made by the oracle's encoder are imported
+so that the kernels are also checked on metadata the library did not produce.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gpu_decode(R, streams, opts=None, cuda_stream=None, check=True, repeat=1):
+    plan = R.Plan(streams, opts)
+    ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device="cuda")
+    infos = [s.info for s in streams]
+    outs = [torch.full((max(1, i["n_syms"] * i["sym_bytes"]),), 0xAB, dtype=torch.uint8, device="cuda")
+            for i in infos]
+    cs = cuda_stream or torch.cuda.current_stream()
+    plan.upload(ws, stream=cs)
+    for _ in range(repeat):
+        plan.decode([o.data_ptr() for o in outs], cs)
+    flags = plan.errors(cs)
+    if check:
+        assert flags == 0, R.recoil_last_error()
+    res = []
+    for o, i in zip(outs, infos):
+        a = o.cpu().numpy()[: i["n_syms"] * i["sym_bytes"]]
+        res.append(a.view(np.uint16) if i["sym_bytes"] == 2 else a)
+    return (res, flags, plan) if not check else res
+
+
+def _import(R, o: oracle.OracleStream, sym_bytes=1):
+    return R.stream_import(o.n, sym_bytes, o.N, o.f, o.words, o.final, o.q, o.idx[:-1], o.y[:-1])
+
+
+def test_config1_decodes_at_64_16_1_splits(recoil_lib):
+    R = recoil_lib
+    st = workloads.laplace_1mib()
+    s = st.symbols()
+    p = R.encode_with_splits(s, st.n_bits, 64)
+    o = oracle.encode_with_splits(s, st.n_bits, 64)
+    assert p.info["n_entries"] == 64
+    for Mp in (64, 16, 1):
+        c = R.combine_splits(p, Mp)
+        (out,) = gpu_decode(R, [c])
+        assert np.array_equal(out, s)
+        assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(np.uint8))
+
+
+DISTS = [
+    ("laplace", {"mean": 128.0, "scale": 8.0}, 11, 1),
+    ("zipf", {"s": 1.2}, 12, 1),
+    ("skewed", {"p0": 0.95}, 12, 1),
+    ("uniform", {}, 12, 1),
+    ("gauss16", {"mean": 2048.0, "sigma": 200.0, "k": 4096}, 15, 2),
+    ("expbytes", {"lam": 200.0}, 16, 1),
+    ("laplace", {"mean": 128.0, "scale": 30.0}, 13, 1),
+]
+
+
+@pytest.mark.parametrize("dist,params,n,sb", DISTS)
+def test_oracle_made_streams_decode_on_gpu(recoil_lib, dist, params, n, sb):
+    R = recoil_lib
+    s = workloads.Stream("t", 200_003, sb, n, dist, params, seed=31).symbols()
+    o = oracle.encode_with_splits(s, n, 97)
+    want = oracle.decode_splits(o)
+    assert np.array_equal(want, s)
+    (out,) = gpu_decode(R, [_import(R, o, sb)])
+    assert np.array_equal(out.astype(np.uint32), want)
+
+
+def test_random_subsets_of_split_entries(recoil_lib):
+    R = recoil_lib
+    s = workloads.Stream("t", 120_000, 1, 11, "laplace", {"mean": 128.0, "scale": 8.0}, seed=32).symbols()
+    o = oracle.encode_with_splits(s, 11, 300)
+    g = np.random.default_rng(5)
+    streams = []
+    for t in range(24):
+        keep = np.sort(g.choice(o.K - 1, size=int(g.integers(0, o.K - 1)), replace=False))
+        sub = oracle.OracleStream(o.N, o.n, o.W, o.lgL, o.b, o.f, o.words, o.final, o.ev_sym, o.ev_y,
+                                  o.q[keep], np.vstack([o.idx[keep], o.idx[-1:]]), np.vstack([o.y[keep], o.y[-1:]]))
+        assert np.array_equal(oracle.decode_splits(sub), s)
+        streams.append(_import(R, sub))
+    outs = gpu_decode(R, streams)
+    for out in outs:
+        assert np.array_equal(out, s)
+
+
+@pytest.mark.parametrize("N", [0, 1, 5, 31, 32, 33, 64, 95, 1000, 4097, 65_539])
+@pytest.mark.parametrize("M", [1, 2, 7, 64])
+def test_edge_lengths(recoil_lib, N, M):
+    R = recoil_lib
+    s = workloads.Stream("t", max(N, 1), 1, 9, "laplace", {"mean": 128.0, "scale": 4.0}, seed=N + 3).symbols()[:N]
+    p = R.encode_with_splits(s, 9, M)
+    (out,) = gpu_decode(R, [p])
+    assert np.array_equal(out, s)
+
+
+@pytest.mark.parametrize("n,sb", [(1, 1), (12, 1), (16, 1), (15, 2), (16, 2)])
+def test_single_symbol_streams(recoil_lib, n, sb):
+    R = recoil_lib
+    s = np.full(10_001, 3, dtype=np.uint8 if sb == 1 else np.uint16)
+    (out,) = gpu_decode(R, [R.encode_with_splits(s, n, 8)])
+    assert np.array_equal(out, s)
+
+
+def _batch_streams(R, count=60, seed=40):
+    g = np.random.default_rng(seed)
+    syms, streams = [], []
+    for k in range(count):
+        N = int(g.integers(0, 300_000)) if k % 7 else int(g.integers(0, 100))
+        kind = k % 5
+        if kind == 4:
+            st = workloads.Stream("g", max(N, 1), 2, 15, "gauss16", {"mean": 2048.0, "sigma": 150.0, "k": 4096}, seed=k)
+        elif kind == 3:
+            st = workloads.Stream("e", max(N, 1), 1, 16, "expbytes", {"lam": 100.0}, seed=k)
+        else:
+            st = workloads.Stream("l", max(N, 1), 1, 12, "laplace", {"mean": 128.0, "scale": float(g.uniform(2, 64))}, seed=k)
+        s = st.symbols()[:N]
+        syms.append(s)
+        streams.append(R.encode_with_splits(s, st.n_bits, max(1, N // 4096)))
+    return syms, streams
+
+
+@pytest.mark.parametrize("opts", [
+    None,
+    {"warps_per_cta": 4},
+    {"warps_per_cta": 8, "ctas_per_sm": 2},
+    {"warps_per_cta": 32},
+    {"warps_per_cta": 1},
+    {"split_symbols": 16384},
+    {"warps_per_cta": 4, "flags": 1},            # one launch per stream
+    {"flags": 2},                                # stream-major order
+])
+def test_batch_of_uneven_streams(recoil_lib, opts):
+    R = recoil_lib
+    syms, streams = _batch_streams(R)
+    outs = gpu_decode(R, streams, opts)
+    for s, out in zip(syms, outs):
+        assert np.array_equal(out, s)
+
+
+def test_batch_graph_replay_and_new_outputs(recoil_lib):
+    R = recoil_lib
+    syms, streams = _batch_streams(R, count=30, seed=41)
+    plan = R.Plan(streams, {"flags": R.BATCH_GRAPH})
+    ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.Stream()
+    with torch.cuda.stream(cs):
+        plan.upload(ws, stream=cs)
+        for rep in range(3):
+            outs = [torch.zeros(max(1, len(s) * s.itemsize), dtype=torch.uint8, device="cuda") for s in syms]
+            for _ in range(2):
+                plan.decode([o.data_ptr() for o in outs], cs)
+            assert plan.errors(cs) == 0
+            for s, o in zip(syms, outs):
+                a = o.cpu().numpy()[: len(s) * s.itemsize]
+                assert np.array_equal(a.view(s.dtype), s)
+    assert plan.launches >= 1
+
+
+def test_one_shot_decode_and_batch_entry_points(recoil_lib):
+    R = recoil_lib
+    syms, streams = _batch_streams(R, count=12, seed=42)
+    need = R.workspace_size(streams)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    outs = [torch.zeros(max(1, len(s) * s.itemsize), dtype=torch.uint8, device="cuda") for s in syms]
+    cs = torch.cuda.current_stream()
+    R.decode_batch(streams, [o.data_ptr() for o in outs], ws, need, cs)
+    torch.cuda.synchronize()
+    for s, o in zip(syms, outs):
+        assert np.array_equal(o.cpu().numpy()[: len(s) * s.itemsize].view(s.dtype), s)
+    one = R.workspace_size([streams[1]])
+    out1 = torch.zeros(max(1, len(syms[1]) * syms[1].itemsize), dtype=torch.uint8, device="cuda")
+    R.decode(streams[1], out1, ws, one, cs)
+    torch.cuda.synchronize()
+    assert np.array_equal(out1.cpu().numpy()[: len(syms[1]) * syms[1].itemsize].view(syms[1].dtype), syms[1])
+    with pytest.raises(R.RecoilError):
+        R.decode(streams[1], out1, ws, 16, cs)                # workspace too small
+
+
+def test_corrupt_words_raise_an_error_flag_not_a_fault(recoil_lib):
+    """Corruption made on the host; the kernel's loops are bounded, so it reports, never hangs."""
+    R = recoil_lib
+    s = workloads.Stream("t", 50_000, 1, 11, "laplace", {"mean": 128.0, "scale": 8.0}, seed=43).symbols()
+    o = oracle.encode_with_splits(s, 11, 4)
+    bad = o.words.copy()
+    bad[len(bad) // 3: len(bad) // 3 + 50] ^= 0x5A5A
+    st = R.stream_import(11, 1, o.N, o.f, bad, o.final, o.q, o.idx[:-1], o.y[:-1])
+    outs, flags, plan = gpu_decode(R, [st], check=False)
+    assert flags != 0
+    short = R.stream_import(11, 1, o.N, o.f, o.words[: len(o.words) // 2], o.final, [], np.zeros((0, 32)),
+                            np.zeros((0, 32)))
+    outs, flags, plan = gpu_decode(R, [short], check=False)
+    assert flags != 0
+    # the context is still usable
+    (out,) = gpu_decode(R, [_import(R, o)])
+    assert np.array_equal(out, s)
+
+
+@pytest.mark.parametrize("target", [148, 592, 2368, 9472])
+def test_zipf_1gib_full_size(recoil_lib, zipf_1gib, target):
+    """1 GiB Zipf(1.2), n = 12, encoded at 65536 splits, combined as the benchmark sweeps."""
+    R = recoil_lib
+    s_dev, stream, s = zipf_1gib
+    c = R.combine_splits(stream, target)
+    plan = R.Plan([c])
+    ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device="cuda")
+    out = torch.empty(len(s), dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.current_stream()
+    plan.upload(ws, stream=cs)
+    plan.decode([out.data_ptr()], cs)
+    assert plan.errors(cs) == 0
+    assert torch.equal(out, s_dev)
+    # sampled threads against the oracle, one by one
+    e = c.export()
+    info = c.info
+    K = info["n_entries"]
+    for k in (0, K // 2, K - 1):
+        lo = 0 if k == 0 else int(e["entry_index"][k - 1].min())
+        hi = len(s) - 1 if k == K - 1 else int(e["entry_index"][k].min()) - 1
+        if hi - lo > 10_000_000:
+            continue
+        ost = oracle.OracleStream(len(s), 12, 32, 16, 16, e["freq"], e["words"], e["final"], None, None,
+                                  e["entry_word"].astype(np.int64),
+                                  np.vstack([e["entry_index"].astype(np.int64), np.zeros((1, 32), np.int64)]),
+                                  np.vstack([e["entry_state"].astype(np.uint32), e["final"][None, :]]))
+        want = oracle.decode_thread(ost, k)[lo:hi + 1]
+        assert np.array_equal(out[lo:hi + 1].cpu().numpy(), want.astype(np.uint8))
+
+
+@pytest.fixture(scope="module")
+def zipf_1gib(recoil_lib):
+    st = workloads.zipf_1gib()
+    s = st.symbols()
+    stream = recoil_lib.encode_with_splits(s, st.n_bits, 65536)
+    assert stream.info["n_entries"] == 65536
+    return torch.from_numpy(s).cuda(), stream, s

@@ -1,0 +1,107 @@
+"""Host side of the library against the oracle (no GPU).
+
+The library's encoder, split placement and combiner are separate code from
+the oracle's, written to the same rules (quantiser reading, Eqs. 1 and 3,
+Sec. 4.1 backward scan, Def. 4.1 / Eq. 7, Sec. 3.3 combining). Everything is
+integer, so parity is bit-exact: frequency table, words, final states, split
+words, recorded indices and states.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+
+def _cases():
+    yield workloads.laplace_1mib()
+    yield workloads.Stream("zipf", 300_001, 1, 12, "zipf", {"s": 1.2}, seed=21)
+    yield workloads.Stream("skewed", 200_003, 1, 12, "skewed", {"p0": 0.95}, seed=22)
+    yield workloads.Stream("uniform", 100_000, 1, 12, "uniform", {}, seed=23)
+    yield workloads.Stream("gauss16", 150_017, 2, 15, "gauss16", {"mean": 2048.0, "sigma": 200.0, "k": 4096}, seed=24)
+    yield workloads.Stream("exp_n16", 120_000, 1, 16, "expbytes", {"lam": 200.0}, seed=25)
+    yield workloads.Stream("lap_n8", 70_001, 1, 8, "laplace", {"mean": 128.0, "scale": 3.0}, seed=26)
+
+
+def _same(R, s, n, M):
+    p = R.encode_with_splits(s, n, M)
+    o = oracle.encode_with_splits(s, n, M, alphabet=None)
+    e = p.export()
+    assert np.array_equal(e["freq"], o.f)
+    assert np.array_equal(e["words"], o.words)
+    assert np.array_equal(e["final"], o.final)
+    assert np.array_equal(e["entry_word"].astype(np.int64), o.q)
+    assert np.array_equal(e["entry_index"].astype(np.int64), o.idx[:-1])
+    assert np.array_equal(e["entry_state"].astype(np.uint32), o.y[:-1])
+    return p, o
+
+
+@pytest.mark.parametrize("st", list(_cases()), ids=lambda s: s.name)
+@pytest.mark.parametrize("M", [1, 2, 64, 1000])
+def test_encoder_matches_oracle(recoil_lib, st, M):
+    _same(recoil_lib, st.symbols(), st.n_bits, M)
+
+
+@pytest.mark.parametrize("N", [0, 1, 2, 31, 32, 33, 63, 64, 65, 100, 1023])
+@pytest.mark.parametrize("M", [1, 3, 16])
+def test_edge_lengths_match_oracle(recoil_lib, N, M):
+    s = workloads.Stream("t", max(N, 1), 1, 10, "laplace", {"mean": 128.0, "scale": 2.0}, seed=N).symbols()[:N]
+    if N == 0:
+        p = recoil_lib.encode_with_splits(s, 10, M)
+        assert p.info["n_words"] == 0 and p.info["n_entries"] == 1
+        return
+    _same(recoil_lib, s, 10, M)
+
+
+@pytest.mark.parametrize("sym", [0, 7, 255])
+@pytest.mark.parametrize("n", [1, 12, 16])
+def test_single_symbol_stream(recoil_lib, sym, n):
+    s = np.full(5000, sym, dtype=np.uint8)
+    p, o = _same(recoil_lib, s, n, 8)
+    assert p.info["n_words"] == 0 and p.info["n_entries"] == 1      # f = 2^n never renormalises
+    assert np.all(o.final == 1 << 16)
+
+
+@pytest.mark.parametrize("K,Mp", [(64, 16), (64, 1), (64, 64), (64, 100), (37, 5), (9472, 148)])
+def test_combine_matches_oracle_rule(recoil_lib, K, Mp):
+    s = workloads.Stream("t", K * 600, 1, 11, "laplace", {"mean": 128.0, "scale": 8.0}, seed=K).symbols()
+    p = recoil_lib.encode_with_splits(s, 11, K)
+    assert p.info["n_entries"] == K
+    c = recoil_lib.combine_splits(p, Mp)
+    keep = oracle.combine_keep(K, Mp)
+    ep, ec = p.export(), c.export()
+    regular = [k for k in keep if k < K - 1]
+    assert c.info["n_entries"] == len(keep)
+    assert np.array_equal(ec["entry_word"], ep["entry_word"][regular])
+    assert np.array_equal(ec["entry_index"], ep["entry_index"][regular])
+    assert np.array_equal(ec["words"], ep["words"])
+
+
+def test_import_round_trip_and_validation(recoil_lib):
+    R = recoil_lib
+    st = workloads.laplace_1mib(1 << 16)
+    o = oracle.encode_with_splits(st.symbols(), 11, 8)
+    args = dict(n_bits=11, sym_bytes=1, n_syms=o.N, freq=o.f, words=o.words, final=o.final,
+                entry_word=o.q, entry_index=o.idx[:-1], entry_state=o.y[:-1])
+    s = R.stream_import(**args)
+    e = s.export()
+    assert np.array_equal(e["words"], o.words) and np.array_equal(e["entry_word"].astype(np.int64), o.q)
+
+    def bad(**kw):
+        a = dict(args)
+        a.update(kw)
+        with pytest.raises(R.RecoilError) as err:
+            R.stream_import(**a)
+        return err.value.code
+
+    f = o.f.copy()
+    f[0] += 1
+    assert bad(freq=f) == R.ECORRUPT                               # does not sum to 2^n
+    idx = o.idx[:-1].copy()
+    idx[0, 3] += 1
+    assert bad(entry_index=idx) == R.ECORRUPT                      # not congruent to its coder
+    assert bad(entry_word=o.q[::-1].copy()) == R.ECORRUPT          # words not increasing
+    fin = o.final.copy()
+    fin[5] = 10
+    assert bad(final=fin) == R.ECORRUPT                            # final state below L
+    assert bad(n_bits=17) == R.EINVAL
