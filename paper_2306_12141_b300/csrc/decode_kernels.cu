@@ -145,7 +145,12 @@ struct EntryDecoder {
   }
 
   // A group step with per-lane predicates (synchronisation phase and range edges).
-  __device__ __forceinline__ void pstep(Walker& w, int g, int act, uint32_t x0, int lo, int hi1) {
+  // At the group where coder j of the previous entry joined (act_p), the
+  // state right after decoding must be that entry's recorded state x_p: the
+  // previous split's metadata is exactly the state this thread carries across
+  // the boundary (Sec. 3.1, 4.1.3), so any corrupt word or state shows here.
+  __device__ __forceinline__ void pstep(Walker& w, int g, int act, uint32_t x0, int lo, int hi1,
+                                        int act_p, uint32_t x_p, bool& bad) {
     const int i = g * kW + lane;
     const bool dec = (g < act) && (i >= lo);
     const bool join = (g == act);
@@ -154,6 +159,7 @@ struct EntryDecoder {
       if (i < hi1) out[i] = (typename SymOut<KIND>::T)s;
     }
     if (join) w.x = x0;
+    if (g == act_p && w.x != x_p) bad = true;
     renorm(w, (dec || join) && w.x < kL);
     w.rp = (w.p & (kRingWords - 1)) + kRingWords;
     if (w.p < w.cbase) refill(w);
@@ -191,9 +197,18 @@ struct EntryDecoder {
     const int g_lo = lo >> 5;
     const int g_full = __reduce_min_sync(kFull, act);            // below it every coder has joined
     const int steady_hi = min(g_full - 1, (hi1 >> 5) - 1);       // whole groups owned ...
-    const int steady_lo = (lo + kW - 1) >> 5;                    // ... and fully decodable
+    // the previous entry of the same stream (there is one whenever lo > 0)
+    int act_p = -1, gtop_p = -1;
+    uint32_t x_p = 0;
+    if (lo > 0) {
+      act_p = ent[-1].act[lane];
+      x_p = ent[-1].x0[lane];
+      gtop_p = ent[-1].g_top;
+    }
+    const int steady_lo = max((lo + kW - 1) >> 5, gtop_p + 1);   // ... fully decodable, above the check
+    bool bad = false;
 
-    for (; g > steady_hi && g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1);
+    for (; g > steady_hi && g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
 
     if (g >= steady_lo) {
       typename SymOut<KIND>::T* o = out + (size_t)g * kW + lane;
@@ -215,12 +230,13 @@ struct EntryDecoder {
       }
     }
 
-    for (; g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1);
+    for (; g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
 
     // The first thread of a stream must end where the encoder started (Eqs. 1-4 invert).
     uint32_t err = 0;
     if (w.p < -1) err |= kErrUnderrun;
     if (lo == 0 && (w.p != -1 || __any_sync(kFull, w.x != kL))) err |= kErrCorrupt;
+    if (__any_sync(kFull, bad)) err |= kErrCorrupt;
     if (err && lane == 0) {
       atomicOr(&ctl->errors, err);
       atomicExch(&ctl->bad_entry, entry_id + 1);

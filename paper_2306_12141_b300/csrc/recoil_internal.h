@@ -106,7 +106,8 @@ struct alignas(16) DevControl {
 static_assert(sizeof(DevControl) == 256, "DevControl layout");
 
 // Error flags raised by kernels.
-constexpr uint32_t kErrCorrupt = 1u;         // first thread did not end at p = -1 with all states = L
+constexpr uint32_t kErrCorrupt = 1u;         // a state differs from the previous entry's record, or the
+                                             // first thread did not end at p = -1 with every state = L
 constexpr uint32_t kErrUnderrun = 2u;        // a read went below word 0
 
 // Arguments of one kernel launch.

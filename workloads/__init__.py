@@ -104,6 +104,13 @@ def _chunks(n: int):
     return [(s, min(CHUNK, n - s)) for s in range(0, n, CHUNK)]
 
 
+def _seedseq(seed) -> np.random.SeedSequence:
+    """A fresh SeedSequence for seed (copied, since spawning advances a sequence's counter)."""
+    if isinstance(seed, np.random.SeedSequence):
+        return np.random.SeedSequence(seed.entropy, spawn_key=seed.spawn_key, pool_size=seed.pool_size)
+    return np.random.SeedSequence(seed)
+
+
 def _threads() -> int:
     return max(1, min(32, os.cpu_count() or 1))
 
@@ -113,7 +120,7 @@ def sample_pmf(pmf: np.ndarray, n: int, seed, threads: int | None = None) -> np.
     table = cell_table(pmf)
     out = np.empty(n, dtype=table.dtype)
     parts = _chunks(n)
-    kids = np.random.SeedSequence(seed).spawn(max(1, len(parts)))
+    kids = _seedseq(seed).spawn(max(1, len(parts)))
 
     def fill(k):
         s, m = parts[k]
@@ -134,7 +141,7 @@ def sample_uniform(n: int, seed, k: int = 256, threads: int | None = None) -> np
     dtype = np.uint8 if k <= 256 else np.uint16
     out = np.empty(n, dtype=dtype)
     parts = _chunks(n)
-    kids = np.random.SeedSequence(seed).spawn(max(1, len(parts)))
+    kids = _seedseq(seed).spawn(max(1, len(parts)))
 
     def fill(c):
         s, m = parts[c]
