@@ -259,10 +259,14 @@ static int64_t iabs(int64_t v) { return v < 0 ? -v : v; }
 
 /*
  * Split heuristic (Def. 4.1, Eq. 7). Chooses up to M-1 split words q[0..) in
- * increasing order; the final states make the M-th split. For each split,
- * with lo = the previous split's smallest recorded index (0 for the first),
+ * increasing order; the final states make the M-th split. For split k, with
+ * lo = the previous split's smallest recorded index (0 for the first),
  * t = top + 1 - lo and t_s = top + 1 - m, the word minimising
- * H = |t - T| + |t - t_s - T|, T = ceil(N / M), is taken (ties: smaller word).
+ * H = |t - T| + |t - t_s - T| is taken (ties: smaller word). T is the
+ * expected number of symbols per split, taken over what is left:
+ * T = ceil((N - lo) / (M - k)), which is ceil(N / M) for the first split.
+ * (With ceil(N / M) throughout, each split falls short of T by about half
+ * its synchronisation section and the shortfall piles up in the final split.)
  * The scan for one split stops once m - lo - T exceeds the best H so far,
  * since m never decreases with the word offset. Returns the number of split
  * words written to q_out (at most M-1).
@@ -270,11 +274,11 @@ static int64_t iabs(int64_t v) { return v < 0 ? -v : v; }
 int64_t oracle_heuristic(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw, int64_t N,
                          int W, int64_t M, int64_t *q_out) {
     if (M < 1 || W < 1 || W > 64) return OR_EINVAL;
-    int64_t T = (N + M - 1) / M;
     int64_t idx[64], wp[64];
     uint32_t y[64];
     int64_t count = 0, lo = 0, qprev = -1;
     while (count < M - 1) {
+        int64_t T = (N - lo + (M - count) - 1) / (M - count);
         int64_t best = -1, bestH = 0, best_m = 0;
         for (int64_t q = qprev + 1; q < nw; q++) {
             if (!oracle_scan(ev_sym, ev_y, q, W, idx, y, wp)) continue;

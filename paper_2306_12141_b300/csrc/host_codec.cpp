@@ -147,7 +147,6 @@ void place_splits(const Records& rec, uint64_t N, uint32_t M, std::vector<uint64
   out.clear();
   const int64_t nw = (int64_t)rec.sym.size();
   if (M < 2 || nw == 0) return;
-  const int64_t T = (int64_t)((N + M - 1) / M);
   int64_t last[kW];
   int seen = 0;
   for (int j = 0; j < kW; j++) last[j] = std::numeric_limits<int64_t>::min();
@@ -168,6 +167,9 @@ void place_splits(const Records& rec, uint64_t N, uint32_t M, std::vector<uint64
 
   int64_t lo = 0, q = 0;
   while (out.size() + 1 < M) {
+    // expected symbols per split over what is left (ceil(N / M) for the first split)
+    const int64_t left = (int64_t)M - (int64_t)out.size();
+    const int64_t T = ((int64_t)N - lo + left - 1) / left;
     int64_t best = -1, bestH = 0;
     for (; q < nw; q++) {
       apply(q);
