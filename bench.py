@@ -55,6 +55,11 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", default="batch", choices=["batch", "zipf"])
+    ap.add_argument("--splits", type=int, default=9472, help="zipf: decoder split count")
+    ap.add_argument("--sweep", type=lambda v: [int(x) for x in v.split(",") if x], default=[148, 592, 2368, 9472],
+                    help="zipf: split counts to sweep (empty to skip)")
+    ap.add_argument("--soak", type=float, default=1.0, help="seconds of untimed steps while sampling clocks")
     return ap.parse_args()
 
 
@@ -205,6 +210,21 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------- our arm
+ZIPF_WORKLOAD = ("single stream: 1 GiB of Zipf(s=1.2) bytes over 256 symbols, n=12, W=32, encoded at 65536 "
+                 "splits and combined to the decoder's split count")
+
+
+def make_workload(a, R, rank):
+    """(description, specs, symbols, encoded streams, streams to decode) of the chosen workload."""
+    if a.workload == "batch":
+        specs, syms, streams = build_batch(R, a.streams, a.scale, rank)
+        return BATCH_WORKLOAD, specs, syms, streams, streams
+    st = workloads.zipf_1gib(int((1 << 30) * a.scale))
+    s = st.symbols()
+    enc = R.encode_with_splits(s, st.n_bits, max(1, min(65536, len(s) // 4096)))
+    return ZIPF_WORKLOAD, [st], [s], [enc], [R.combine_splits(enc, a.splits)]
+
+
 def run_ours(a):
     import torch
     import paper_2306_12141_b300 as R
@@ -219,13 +239,14 @@ def run_ours(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    specs, syms, streams = build_batch(R, a.streams, a.scale, rank)
+    desc, specs, syms, encoded, streams = make_workload(a, R, rank)
     out_bytes = sum(len(s) * s.itemsize for s in syms)
     in_bytes = sum(2 * st.info["n_words"] + 4 * 32 for st in streams)
+    batch = a.workload == "batch"
 
-    split_symbols = 65536 if a.split_symbols < 0 else a.split_symbols
-    opts = {"warps_per_cta": a.warps or 16, "ctas_per_sm": a.ctas_per_sm,
-            "split_symbols": split_symbols, "flags": 4}
+    split_symbols = (65536 if a.split_symbols < 0 else a.split_symbols) if batch else 0
+    opts = {"warps_per_cta": a.warps or (8 if batch else 16), "ctas_per_sm": a.ctas_per_sm,
+            "split_symbols": split_symbols, "flags": R.BATCH_GRAPH}
     plan = R.Plan(streams, opts)
     ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
     outs = [torch.empty(max(1, len(s) * s.itemsize), dtype=torch.uint8, device=dev) for s in syms]
@@ -251,30 +272,56 @@ def run_ours(a):
         barrier()
         return [e0.elapsed_time(e1) for e0, e1 in ev]
 
-    with torch.cuda.stream(cs):
-        plan.upload(ws, stream=cs)
-        with Clocks(local) as clk:
-            ms = timed(lambda: plan.decode(out_ptrs, cs), a.steps, a.warmup)
-        clocks = clk.summary()
-        launches = plan.launches
-        assert plan.errors(cs) == 0, R.recoil_last_error()
-        # the last timed decode must reproduce every stream exactly (device compare)
+    def exact():
         bad = 0
         for s, o in zip(syms, outs):
             if len(s) and not torch.equal(o[: len(s) * s.itemsize], torch.from_numpy(s.view(np.uint8)).to(dev)):
                 bad += 1
         assert bad == 0, f"{bad} streams decoded wrong"
 
-        # per-stream baseline: one launch per stream, 128-thread blocks, all encoded splits
-        base = R.Plan(streams, {"warps_per_cta": 4, "flags": 1})
-        bws = torch.empty(base.workspace_size, dtype=torch.uint8, device=dev)
-        base.upload(bws, stream=cs)
-        base_ms = timed(lambda: base.decode(out_ptrs, cs), a.per_stream_steps, 1)
-        assert base.errors(cs) == 0
-        base_launches = base.launches
-        del bws
+    extra = {}
+    with torch.cuda.stream(cs):
+        plan.upload(ws, stream=cs)
+        decode = lambda: plan.decode(out_ptrs, cs)  # noqa: E731
+        with Clocks(local) as clk:
+            t_end = time.time() + a.soak                 # keep the step running so the sampler sees load
+            while time.time() < t_end:
+                decode()
+                torch.cuda.synchronize()
+            ms = timed(decode, a.steps, a.warmup)
+        clocks = clk.summary()
+        clocks["note"] = f"sampled every 100 ms over a {a.soak:.1f} s soak of the same step and the timed steps"
+        launches = plan.launches
+        assert plan.errors(cs) == 0, R.recoil_last_error()
+        exact()                                           # the last timed decode reproduces every stream
 
-        # end to end through the public API: H2D from pinned host memory, decode, D2H of the symbols
+        if batch and a.per_stream_steps > 0:
+            # per-stream baseline: one launch per stream, 128-thread blocks, every encoded split
+            base = R.Plan(streams, {"warps_per_cta": 4, "flags": R.BATCH_PER_STREAM})
+            bws = torch.empty(base.workspace_size, dtype=torch.uint8, device=dev)
+            base.upload(bws, stream=cs)
+            base_ms = timed(lambda: base.decode(out_ptrs, cs), a.per_stream_steps, 1)
+            assert base.errors(cs) == 0
+            exact()
+            extra["per_stream"] = {"value": out_bytes / (statistics.mean(base_ms) * 1e-3) / 1e9, "unit": "GB/s",
+                                   "ms_per_step": statistics.mean(base_ms), "launches_per_step": base.launches,
+                                   "speedup": statistics.mean(base_ms) / statistics.mean(ms)}
+            del bws
+
+        if not batch and a.sweep:
+            sweep = {}
+            for k in a.sweep:
+                c = R.combine_splits(encoded[0], k)
+                sp = R.Plan([c], {"warps_per_cta": opts["warps_per_cta"], "flags": R.BATCH_GRAPH})
+                sws = torch.empty(sp.workspace_size, dtype=torch.uint8, device=dev)
+                sp.upload(sws, stream=cs)
+                t = timed(lambda: sp.decode(out_ptrs, cs), 5, 2)
+                assert sp.errors(cs) == 0
+                sweep[str(c.info["n_entries"])] = round(out_bytes / (statistics.mean(t) * 1e-3) / 1e9, 1)
+                del sws
+            exact()
+            extra["split_sweep_gbs"] = sweep
+
         e2e = None
         if not a.no_e2e:
             for st in streams:
@@ -284,7 +331,6 @@ def run_ours(a):
             offs = np.concatenate([[0], np.cumsum([max(1, len(s) * s.itemsize) for s in syms])])
             flat = torch.empty(int(offs[-1]), dtype=torch.uint8, device=dev)
             flat_ptrs = [flat.data_ptr() + int(o) for o in offs[:-1]]
-            h2d = ep.workspace_size
 
             def e2e_step():
                 ep.upload(ws, stream=cs)
@@ -292,8 +338,10 @@ def run_ours(a):
                 host_out.copy_(flat[:out_bytes], non_blocking=True)
 
             e_ms = timed(e2e_step, max(2, a.steps // 2), 1)
-            e2e = {"value": out_bytes / (statistics.mean(e_ms) * 1e-3) / 1e9, "unit": "GB/s",
-                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_bytes)}
+            assert ep.errors(cs) == 0
+            e2e = {"value": world * out_bytes / (statistics.mean(e_ms) * 1e-3) / 1e9, "unit": "GB/s",
+                   "h2d_bytes_per_step": int(ep.workspace_size), "d2h_bytes_per_step": int(out_bytes),
+                   "ms_per_step": statistics.mean(e_ms)}
             del flat
 
     mean_ms = statistics.mean(ms)
@@ -308,23 +356,26 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD,
-                   "symbols_bytes": out_bytes, "compressed_bytes": in_bytes,
+        "config": {"workload": desc, "symbols_bytes": out_bytes, "compressed_bytes": in_bytes,
+                   "splits": sum(st.info["n_entries"] for st in plan.streams) if not batch else None,
                    "split_symbols": split_symbols, "warps_per_cta": opts["warps_per_cta"],
                    "parallelism": f"weak x{world}", "l2": "inputs larger than L2 (no flush)",
                    "scale": a.scale},
-        "per_stream": {"value": out_bytes / (statistics.mean(base_ms) * 1e-3) / 1e9, "unit": "GB/s",
-                       "ms_per_step": statistics.mean(base_ms), "launches": base_launches,
-                       "speedup": statistics.mean(base_ms) / mean_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "peak_source": peaks["source"], "kernel": "decode_kernel<kPacked8>"},
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                     "kernel": "decode_kernel<kPacked8>", "bytes": "compressed words in + symbols out"},
         "clocks": clocks,
         "gpu_launches": launches * a.steps,
         "e2e": e2e,
     }
+    line.update(extra)
     if rank == 0 and not a.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(specs, syms, a.cpu_seconds)
+        if batch:
+            line["cpu_baseline"] = cpu_baseline(specs, syms, a.cpu_seconds)
+        else:                                             # the oracle sees the stream in 16 Mi-symbol pieces
+            piece = 1 << 24
+            parts = [syms[0][i:i + piece] for i in range(0, min(len(syms[0]), 64 * piece), piece)]
+            line["cpu_baseline"] = cpu_baseline([specs[0]] * len(parts), parts, a.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -244,8 +244,20 @@ struct EntryDecoder {
   }
 };
 
-template <uint32_t KIND>
-__global__ void __launch_bounds__(1024) decode_kernel(const LaunchArgs a) {
+// Blocks of WARPS warps; the second launch bound asks for enough resident
+// blocks to keep RECOIL_RESIDENT_WARPS warps per SM, which caps registers at
+// 65536 / (32 * RECOIL_RESIDENT_WARPS) a thread.
+#ifndef RECOIL_RESIDENT_WARPS
+#define RECOIL_RESIDENT_WARPS 48
+#endif
+template <int WARPS>
+struct Residency {
+  static constexpr int kWant = RECOIL_RESIDENT_WARPS / WARPS;
+  static constexpr int kMinBlocks = kWant < 1 ? 1 : (kWant > 32 ? 32 : kWant);
+};
+
+template <uint32_t KIND, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, Residency<WARPS>::kMinBlocks) decode_kernel(const LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item;
   const int warp = threadIdx.x >> 5;
@@ -265,7 +277,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(const LaunchArgs a) {
       const uint4* src = reinterpret_cast<const uint4*>(a.table_pool + st.table);
       uint4* dst = reinterpret_cast<uint4*>(smem);
       const uint32_t n16 = st.table_bytes >> 4;
-      for (uint32_t k = threadIdx.x; k < n16; k += blockDim.x) dst[k] = __ldg(src + k);
+      for (uint32_t k = threadIdx.x; k < n16; k += WARPS * 32) dst[k] = __ldg(src + k);
       staged = item.stream;
       __syncthreads();
     }
@@ -286,44 +298,71 @@ __global__ void __launch_bounds__(1024) decode_kernel(const LaunchArgs a) {
   }
 }
 
-template <uint32_t KIND>
 size_t smem_bytes(uint32_t warps, uint32_t table_smem) {
   return (size_t)table_smem + (size_t)warps * kRingSlots * sizeof(uint16_t);
 }
 
-template <uint32_t KIND>
-cudaError_t launch_kind(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  const size_t sm = smem_bytes<KIND>(a.warps, a.table_smem);
-  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <uint32_t KIND, int WARPS>
+cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  const size_t sm = smem_bytes(WARPS, a.table_smem);
+  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  decode_kernel<KIND><<<grid, a.warps * 32, sm, s>>>(a);
+  decode_kernel<KIND, WARPS><<<grid, WARPS * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-template <uint32_t KIND>
-int occupancy_kind(uint32_t warps, uint32_t table_smem, int* out) {
-  const size_t sm = smem_bytes<KIND>(warps, table_smem);
-  if (cudaFuncSetAttribute(decode_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+template <uint32_t KIND, int WARPS>
+int occupancy_kw(uint32_t table_smem, int* out) {
+  const size_t sm = smem_bytes(WARPS, table_smem);
+  if (cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return -1;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND>, (int)warps * 32, sm) == cudaSuccess ? 0 : -1;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
+}
+
+template <uint32_t KIND>
+cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  switch (a.warps) {
+    case 1: return launch_kw<KIND, 1>(a, grid, s);
+    case 2: return launch_kw<KIND, 2>(a, grid, s);
+    case 4: return launch_kw<KIND, 4>(a, grid, s);
+    case 8: return launch_kw<KIND, 8>(a, grid, s);
+    case 16: return launch_kw<KIND, 16>(a, grid, s);
+    case 32: return launch_kw<KIND, 32>(a, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <uint32_t KIND>
+int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
+  switch (warps) {
+    case 1: return occupancy_kw<KIND, 1>(table_smem, out);
+    case 2: return occupancy_kw<KIND, 2>(table_smem, out);
+    case 4: return occupancy_kw<KIND, 4>(table_smem, out);
+    case 8: return occupancy_kw<KIND, 8>(table_smem, out);
+    case 16: return occupancy_kw<KIND, 16>(table_smem, out);
+    case 32: return occupancy_kw<KIND, 32>(table_smem, out);
+  }
+  return -1;
 }
 
 }  // namespace
 
+bool warps_supported(uint32_t w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32; }
+
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   switch (kind) {
-    case kPacked8: return launch_kind<kPacked8>(a, grid, s);
-    case kGeneric8: return launch_kind<kGeneric8>(a, grid, s);
-    case kGeneric16: return launch_kind<kGeneric16>(a, grid, s);
+    case kPacked8: return launch_k<kPacked8>(a, grid, s);
+    case kGeneric8: return launch_k<kGeneric8>(a, grid, s);
+    case kGeneric16: return launch_k<kGeneric16>(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
 int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out) {
   switch (kind) {
-    case kPacked8: return occupancy_kind<kPacked8>(warps, table_smem, out);
-    case kGeneric8: return occupancy_kind<kGeneric8>(warps, table_smem, out);
-    case kGeneric16: return occupancy_kind<kGeneric16>(warps, table_smem, out);
+    case kPacked8: return occupancy_k<kPacked8>(warps, table_smem, out);
+    case kGeneric8: return occupancy_k<kGeneric8>(warps, table_smem, out);
+    case kGeneric16: return occupancy_k<kGeneric16>(warps, table_smem, out);
   }
   return -1;
 }

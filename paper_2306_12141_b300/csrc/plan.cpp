@@ -291,12 +291,15 @@ int recoil_plan_create(const recoil_stream* const* streams, uint32_t count, cons
     std::unique_ptr<recoil_plan> P(new recoil_plan());
     if (opts) P->opts = *opts;
     P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta : 16;
-    if (P->warps < 1 || P->warps > 32) return fail(RECOIL_EINVAL, "warps_per_cta must be in [1, 32]");
+    if (!warps_supported(P->warps)) return fail(RECOIL_EINVAL, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
     for (uint32_t i = 0; i < count; i++) {
       if (!streams[i]) return fail(RECOIL_EINVAL, "null stream");
       const recoil_stream* s = streams[i];
       if (P->opts.split_symbols) {
-        const uint64_t want = std::max<uint64_t>(1, (s->n_syms + P->opts.split_symbols - 1) / P->opts.split_symbols);
+        // about split_symbols per split, rounded up to whole CTAs so that every
+        // work item keeps all its warps busy on splits of equal size
+        uint64_t want = std::max<uint64_t>(1, (s->n_syms + P->opts.split_symbols - 1) / P->opts.split_symbols);
+        want = (want + P->warps - 1) / P->warps * P->warps;
         recoil_stream* c = nullptr;
         int rc = recoil_combine_splits(s, (uint32_t)std::min<uint64_t>(want, 0xffffffffu), &c);
         if (rc) return rc;

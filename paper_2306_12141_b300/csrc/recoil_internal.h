@@ -130,6 +130,7 @@ struct LaunchArgs {
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s);
 int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out);
 size_t ring_smem_per_warp();
+bool warps_supported(uint32_t warps);   // CTA sizes the kernels are built for: 1, 2, 4, 8, 16, 32 warps
 
 // Error reporting (thread-local message).
 int fail(int code, const std::string& msg);
