@@ -89,6 +89,14 @@ struct SymOut<kGeneric16> {
   using T = uint16_t;
 };
 
+// A read-only load kept where it is written (volatile asm is neither merged
+// with an earlier load of the same address nor hoisted).
+__device__ __forceinline__ int ld_keep(const int* p) {
+  int v;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
 // ------------------------------------------------------------- word ring
 // Word w of the stream sits at ring[(w mod 512)] and ring[(w mod 512) + 512];
 // with rp = (p mod 512) + 512, word p - k (0 <= k < 32) is ring[rp - k] for
@@ -132,16 +140,23 @@ struct EntryDecoder {
     __syncwarp();
   }
 
-  // Eq. 4 for the whole warp: coders with `need` read their word in decreasing coder order.
+  // Eq. 4 for the whole warp: coders with `need` read their word in decreasing
+  // coder order. Only the ring position moves; callers catch p up from it.
   __device__ __forceinline__ void renorm(Walker& w, bool need) {
     const uint32_t m = __ballot_sync(kFull, need);
     if (need) {
       const int k = __popc(m & gt);
       w.x = (w.x << 16) | ring[w.rp - k];
     }
-    const int c = __popc(m);
-    w.p -= c;
-    w.rp -= c;
+    w.rp -= __popc(m);
+  }
+
+  // Bring p up to date with the ring position (rp0 = ring position when p was
+  // last exact), renormalise the ring position and refill if p left the chunk.
+  __device__ __forceinline__ void settle(Walker& w, int rp0) {
+    w.p -= rp0 - w.rp;
+    w.rp = (w.p & (kRingWords - 1)) + kRingWords;
+    if (w.p < w.cbase) refill(w);
   }
 
   // A group step with per-lane predicates (synchronisation phase and range edges).
@@ -160,9 +175,9 @@ struct EntryDecoder {
     }
     if (join) w.x = x0;
     if (g == act_p && w.x != x_p) bad = true;
+    const int rp0 = w.rp;
     renorm(w, (dec || join) && w.x < kL);
-    w.rp = (w.p & (kRingWords - 1)) + kRingWords;
-    if (w.p < w.cbase) refill(w);
+    settle(w, rp0);
   }
 
   // A group step where every coder decodes and every symbol is owned.
@@ -173,10 +188,10 @@ struct EntryDecoder {
   }
 
   __device__ void run(const DevEntry* __restrict__ ent, DevControl* ctl, uint32_t entry_id) {
-    const int lo = (int)ent->lo, hi1 = (int)ent->hi1;
+    int lo = (int)ent->lo, hi1 = (int)ent->hi1;
     if (lo >= hi1) return;
-    const uint32_t x0 = ent->x0[lane];
-    const int act = ent->act[lane];
+    int act = ent->act[lane];
+    uint32_t x0 = ent->x0[lane];
     int g = ent->g_top;
 
     Walker w;
@@ -194,7 +209,6 @@ struct EntryDecoder {
     __syncwarp();
     w.rp = (w.p & (kRingWords - 1)) + kRingWords;
 
-    const int g_lo = lo >> 5;
     const int g_full = __reduce_min_sync(kFull, act);            // below it every coder has joined
     const int steady_hi = min(g_full - 1, (hi1 >> 5) - 1);       // whole groups owned ...
     // the previous entry of the same stream (there is one whenever lo > 0)
@@ -208,29 +222,39 @@ struct EntryDecoder {
     const int steady_lo = max((lo + kW - 1) >> 5, gtop_p + 1);   // ... fully decodable, above the check
     bool bad = false;
 
-    for (; g > steady_hi && g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
+    for (; g > steady_hi && g >= (lo >> 5); --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
 
     if (g >= steady_lo) {
       typename SymOut<KIND>::T* o = out + (size_t)g * kW + lane;
-      while (g - 3 >= steady_lo) {
-        sstep(w, o);
-        sstep(w, o - kW);
-        sstep(w, o - 2 * kW);
-        sstep(w, o - 3 * kW);
-        o -= 4 * kW;
-        g -= 4;
-        w.rp = (w.p & (kRingWords - 1)) + kRingWords;
-        if (w.p < w.cbase) refill(w);
+      // 8 steps consume at most 256 words: with p >= cbase at the start of a
+      // block, every read stays inside the two staged chunks
+      while (g - 7 >= steady_lo) {
+        const int rp0 = w.rp;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sstep(w, o - u * kW);
+        o -= 8 * kW;
+        g -= 8;
+        settle(w, rp0);
       }
       for (; g >= steady_lo; --g) {
+        const int rp0 = w.rp;
         sstep(w, o);
         o -= kW;
-        w.rp = (w.p & (kRingWords - 1)) + kRingWords;
-        if (w.p < w.cbase) refill(w);
+        settle(w, rp0);
       }
     }
 
-    for (; g >= g_lo; --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
+    // Reload what the tail needs instead of keeping it live across the steady
+    // loop (non-coherent loads the compiler cannot merge with the first ones).
+    lo = ld_keep(reinterpret_cast<const int*>(&ent->lo));
+    hi1 = ld_keep(reinterpret_cast<const int*>(&ent->hi1));
+    act = ld_keep(&ent->act[lane]);
+    x0 = (uint32_t)ld_keep(reinterpret_cast<const int*>(&ent->x0[lane]));
+    if (lo > 0) {
+      act_p = ld_keep(&ent[-1].act[lane]);
+      x_p = (uint32_t)ld_keep(reinterpret_cast<const int*>(&ent[-1].x0[lane]));
+    }
+    for (; g >= (lo >> 5); --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
 
     // The first thread of a stream must end where the encoder started (Eqs. 1-4 invert).
     uint32_t err = 0;
