@@ -204,6 +204,39 @@ int recoil_decode_batch(const recoil_stream* const* streams, uint32_t count, voi
                         void* d_workspace, size_t ws_bytes, void* cuda_stream,
                         const recoil_batch_opts* opts);
 
+/* --------------------------------------------------------- no allocation */
+
+/* Device bytes the library keeps for recoil_decode_noalloc (per GPU, for the
+ * life of the process). */
+#define RECOIL_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/*
+ * Decode one stream without any device allocation. The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc (or any
+ * allocator built on it) where they decode -- code inside a host framework
+ * that owns all device memory and only lends fixed buffers, or a path where an
+ * allocation might block or fail at the wrong moment. Such a caller passes
+ * device buffers it already holds:
+ *   d_words      the stream's 16-bit words (recoil_stream_export order),
+ *                16-byte aligned, in a buffer of words_bytes >=
+ *                ceil(n_words / 256) * 512 bytes (the tail is never used as data)
+ *   d_out        n_syms * sym_bytes bytes for the symbols
+ * The split descriptors, decoder tables, work-queue counters and error flags
+ * go to one static device array of RECOIL_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until exit. The first call on a device looks up
+ * that array's device address (with that device current), so make it before
+ * any stream capture. Every call shares the array and finds the previous
+ * call's contents there; a call clears the counters and flags it needs, but
+ * calls whose GPU work overlaps (several host threads or CUDA streams) race on
+ * it and must not be made. Allocates nothing on the device (host memory only
+ * for building the descriptors). Returns after the decode has finished on
+ * cuda_stream. Errors: EINVAL (null, small or misaligned d_words, or a stream
+ * whose descriptors and tables exceed the array: combine it to fewer splits),
+ * ECORRUPT (the decoder found an inconsistent stream), ECUDA.
+ */
+int recoil_decode_noalloc(const recoil_stream* stream, const void* d_words, size_t words_bytes, void* d_out,
+                          void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,7 +48,7 @@ EXPORTS = [
     "recoil_stream_import", "recoil_stream_pin", "recoil_free", "recoil_last_error",
     "recoil_plan_create", "recoil_plan_workspace_size", "recoil_plan_upload", "recoil_plan_decode",
     "recoil_plan_errors", "recoil_plan_launches", "recoil_plan_free", "recoil_workspace_size",
-    "recoil_decode", "recoil_decode_batch",
+    "recoil_decode", "recoil_decode_batch", "recoil_decode_noalloc",
 ]
 
 _lib = None
@@ -84,6 +84,7 @@ def lib():
         L.recoil_workspace_size.argtypes = [vp, u32, C.POINTER(BatchOpts), C.POINTER(C.c_size_t)]
         L.recoil_decode.argtypes = [vp, vp, vp, C.c_size_t, vp]
         L.recoil_decode_batch.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(BatchOpts)]
+        L.recoil_decode_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
         _lib = L
     return _lib
 
@@ -317,6 +318,20 @@ def recoil_plan_free(plan: Plan) -> None:
         plan.handle = None
 
 
+NOALLOC_SCRATCH_BYTES = 4 << 20
+
+
+def noalloc_words_bytes(stream: Stream) -> int:
+    """Bytes of the device word buffer recoil_decode_noalloc reads (words padded to 256-word chunks)."""
+    return -(-stream.info["n_words"] // 256) * 512
+
+
+def recoil_decode_noalloc(stream: Stream, d_words, words_bytes: int, d_out, cuda_stream=None) -> None:
+    """Decode without device allocation: words and output are caller device buffers (see recoil.h)."""
+    _check(lib().recoil_decode_noalloc(stream.handle, _ptr(d_words), words_bytes, _ptr(d_out),
+                                       _stream_handle(cuda_stream)))
+
+
 # short aliases
 encode_with_splits = recoil_encode_with_splits
 combine_splits = recoil_combine_splits
@@ -327,3 +342,4 @@ stream_pin = recoil_stream_pin
 workspace_size = recoil_workspace_size
 decode = recoil_decode
 decode_batch = recoil_decode_batch
+decode_noalloc = recoil_decode_noalloc

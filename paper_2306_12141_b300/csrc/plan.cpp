@@ -228,6 +228,25 @@ static int plan_build(recoil_plan* P) {
   return RECOIL_OK;
 }
 
+namespace recoil {
+void plan_image(const recoil_plan* P, PlanImage* o) {
+  o->meta = P->meta.data();
+  o->meta_bytes = P->meta.size();
+  o->off_outs = P->off_outs;
+  o->off_streams = P->off_streams;
+  o->off_items = P->off_items;
+  o->off_entries = P->off_entries;
+  o->tables = P->tables.data();
+  o->table_bytes = P->tables.size();
+  o->warps = P->warps;
+  for (uint32_t k = 0; k < kKinds; k++) {
+    o->kind_first[k] = P->kind_first[k];
+    o->kind_count[k] = P->kind_count[k];
+    o->kind_smem[k] = P->kind_smem[k];
+  }
+}
+}  // namespace recoil
+
 static int cuda_fail(cudaError_t e, const char* what) {
   return fail(RECOIL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }

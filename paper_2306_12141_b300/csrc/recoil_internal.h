@@ -132,6 +132,23 @@ int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, in
 size_t ring_smem_per_warp();
 bool warps_supported(uint32_t warps);   // CTA sizes the kernels are built for: 1, 2, 4, 8, 16, 32 warps
 
+// Host images of a plan (plan.cpp), for entry points that place them in
+// device memory of their own. meta = control, output pointers, stream
+// descriptors, items, entries (offsets relative to meta); tables separate.
+struct PlanImage {
+  const uint8_t* meta;
+  size_t meta_bytes;
+  size_t off_outs, off_streams, off_items, off_entries;
+  const uint8_t* tables;
+  size_t table_bytes;
+  uint32_t warps;
+  uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds];
+};
+}  // namespace recoil
+struct recoil_plan;
+namespace recoil {
+void plan_image(const recoil_plan* plan, PlanImage* out);
+
 // Error reporting (thread-local message).
 int fail(int code, const std::string& msg);
 void clear_error();
