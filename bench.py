@@ -244,14 +244,26 @@ def run_ours(a):
     in_bytes = sum(2 * st.info["n_words"] + 4 * 32 for st in streams)
     batch = a.workload == "batch"
 
-    split_symbols = (65536 if a.split_symbols < 0 else a.split_symbols) if batch else 0
-    opts = {"warps_per_cta": a.warps or (8 if batch else 16), "ctas_per_sm": a.ctas_per_sm,
-            "split_symbols": split_symbols, "flags": R.BATCH_GRAPH}
-    plan = R.Plan(streams, opts)
-    ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
     outs = [torch.empty(max(1, len(s) * s.itemsize), dtype=torch.uint8, device=dev) for s in syms]
     out_ptrs = [o.data_ptr() for o in outs]
     cs = torch.cuda.Stream(device=dev)
+    tuned = None
+    if batch and a.warps == 0 and a.split_symbols < 0:
+        # the library's autotuner picks warps per CTA and the split size on this batch (untimed)
+        tws = torch.empty(R.autotune_workspace_size(streams), dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(cs):
+            best, tms = R.autotune(streams, out_ptrs, tws, tws.numel(), cs, steps=3)
+        tuned = {"warps_per_cta": best["warps_per_cta"], "split_symbols": best["split_symbols"],
+                 "ms": round(tms, 4)}
+        split_symbols, warps = best["split_symbols"], best["warps_per_cta"]
+        del tws
+    else:
+        split_symbols = (65536 if a.split_symbols < 0 else a.split_symbols) if batch else 0
+        warps = a.warps or (8 if batch else 16)
+    opts = {"warps_per_cta": warps, "ctas_per_sm": a.ctas_per_sm, "split_symbols": split_symbols,
+            "flags": R.BATCH_GRAPH}
+    plan = R.Plan(streams, opts)
+    ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
 
     def barrier():
         if dist:
@@ -359,6 +371,7 @@ def run_ours(a):
         "config": {"workload": desc, "symbols_bytes": out_bytes, "compressed_bytes": in_bytes,
                    "splits": sum(st.info["n_entries"] for st in plan.streams) if not batch else None,
                    "split_symbols": split_symbols, "warps_per_cta": opts["warps_per_cta"],
+                   "autotuned": tuned,
                    "parallelism": f"weak x{world}", "l2": "inputs larger than L2 (no flush)",
                    "scale": a.scale},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

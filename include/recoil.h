@@ -204,6 +204,37 @@ int recoil_decode_batch(const recoil_stream* const* streams, uint32_t count, voi
                         void* d_workspace, size_t ws_bytes, void* cuda_stream,
                         const recoil_batch_opts* opts);
 
+/* ----------------------------------------------------------- autotuning */
+
+typedef struct {
+  uint32_t steps;            /* timed decodes per candidate (default 3) */
+  uint32_t flags;            /* RECOIL_TUNE_* */
+  const char* cache_path;    /* text file of tuned results, or NULL for none */
+} recoil_tune_opts;
+
+#define RECOIL_TUNE_REFRESH 1u     /* ignore a cached result and tune again */
+
+/* Workspace bytes recoil_autotune needs for these streams (the largest candidate). */
+int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t count, size_t* bytes);
+
+/*
+ * Choose batch options for these streams by measurement (the batching pattern
+ * of the paper's decoder-adaptive parallelism, Sec. 3.3: the decoder picks the
+ * split count that suits it). Candidates: warps_per_cta in {4, 8, 16} times
+ * split_symbols in {32 Ki, 64 Ki, 128 Ki, 256 Ki}. Each candidate decodes the
+ * streams into d_outs (caller-owned, as for recoil_plan_decode) once untimed
+ * and `steps` times timed with CUDA events on cuda_stream; the lowest median
+ * wins and is written to *best (ctas_per_sm = 0, flags = 0) with its time in
+ * *best_ms (may be NULL). With a cache_path, a result cached for the same GPU
+ * and batch shape is returned without decoding, and new results are appended.
+ * d_workspace: >= recoil_autotune_workspace_size bytes, 256-byte aligned.
+ * Synchronises cuda_stream. Errors: EINVAL, ENOMEM (workspace too small),
+ * ECORRUPT, ECUDA.
+ */
+int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* const* d_outs, void* d_workspace,
+                    size_t ws_bytes, void* cuda_stream, const recoil_tune_opts* opts, recoil_batch_opts* best,
+                    float* best_ms);
+
 /* --------------------------------------------------------- no allocation */
 
 /* Device bytes the library keeps for recoil_decode_noalloc (per GPU, for the

@@ -43,12 +43,19 @@ class BatchOpts(C.Structure):
                 ("split_symbols", C.c_uint32), ("flags", C.c_uint32)]
 
 
+class TuneOpts(C.Structure):
+    _fields_ = [("steps", C.c_uint32), ("flags", C.c_uint32), ("cache_path", C.c_char_p)]
+
+
+TUNE_REFRESH = 1
+
 EXPORTS = [
     "recoil_encode_with_splits", "recoil_combine_splits", "recoil_stream_info", "recoil_stream_export",
     "recoil_stream_import", "recoil_stream_pin", "recoil_free", "recoil_last_error",
     "recoil_plan_create", "recoil_plan_workspace_size", "recoil_plan_upload", "recoil_plan_decode",
     "recoil_plan_errors", "recoil_plan_launches", "recoil_plan_free", "recoil_workspace_size",
-    "recoil_decode", "recoil_decode_batch", "recoil_decode_noalloc",
+    "recoil_decode", "recoil_decode_batch", "recoil_decode_noalloc", "recoil_autotune",
+    "recoil_autotune_workspace_size",
 ]
 
 _lib = None
@@ -85,6 +92,9 @@ def lib():
         L.recoil_decode.argtypes = [vp, vp, vp, C.c_size_t, vp]
         L.recoil_decode_batch.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(BatchOpts)]
         L.recoil_decode_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
+        L.recoil_autotune_workspace_size.argtypes = [vp, u32, C.POINTER(C.c_size_t)]
+        L.recoil_autotune.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(TuneOpts),
+                                      C.POINTER(BatchOpts), C.POINTER(C.c_float)]
         _lib = L
     return _lib
 
@@ -318,6 +328,23 @@ def recoil_plan_free(plan: Plan) -> None:
         plan.handle = None
 
 
+def recoil_autotune_workspace_size(streams) -> int:
+    n = C.c_size_t()
+    _check(lib().recoil_autotune_workspace_size(_handles(streams), len(streams), C.byref(n)))
+    return n.value
+
+
+def recoil_autotune(streams, outs, workspace, nbytes: int, cuda_stream=None, steps: int = 3,
+                    cache_path: str | None = None, refresh: bool = False) -> tuple[dict, float]:
+    """Measured best batch options for these streams: ({warps_per_cta, split_symbols, ...}, ms)."""
+    t = TuneOpts(steps, TUNE_REFRESH if refresh else 0, cache_path.encode() if cache_path else None)
+    best = BatchOpts()
+    ms = C.c_float()
+    _check(lib().recoil_autotune(_handles(streams), len(streams), _ptr_array(outs), _ptr(workspace), nbytes,
+                                 _stream_handle(cuda_stream), C.byref(t), C.byref(best), C.byref(ms)))
+    return {k: getattr(best, k) for k, _ in BatchOpts._fields_}, float(ms.value)
+
+
 NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
@@ -343,3 +370,5 @@ workspace_size = recoil_workspace_size
 decode = recoil_decode
 decode_batch = recoil_decode_batch
 decode_noalloc = recoil_decode_noalloc
+autotune = recoil_autotune
+autotune_workspace_size = recoil_autotune_workspace_size

@@ -3,8 +3,10 @@
 // upload and launch. A single stream is a batch of one.
 //
 // Workspace layout (caller-owned device memory, every segment 256-B aligned):
-//   control | output pointers | stream descriptors | work items | entries |
-//   decoder tables | words (each stream's words start on a 512-B chunk)
+//   words (each stream's words start on a 512-B chunk) | decoder tables |
+//   control | output pointers | stream descriptors | work items | entries
+// The words and tables depend only on the list of streams, so plans that
+// differ only in how they split the streams share that bulk region.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -113,7 +115,7 @@ struct recoil_plan {
   std::vector<uint8_t> meta;                           // control .. entries
   std::vector<uint8_t> tables;
   size_t off_outs = 0, off_streams = 0, off_items = 0, off_entries = 0;
-  size_t off_tables = 0, off_words = 0, ws_bytes = 0;
+  size_t off_tables = 0, off_meta = 0, ws_bytes = 0;   // words start at 0
   std::vector<uint64_t> word_off;                      // per stream, in words
   uint32_t n_items = 0;
   uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {};
@@ -214,9 +216,9 @@ static int plan_build(recoil_plan* P) {
   P->off_items = P->off_streams + align_up((size_t)count * sizeof(DevStream), kAlign);
   P->off_entries = P->off_items + align_up(items.size() * sizeof(DevItem), kAlign);
   const size_t meta_bytes = P->off_entries + align_up(entries.size() * sizeof(DevEntry), kAlign);
-  P->off_tables = meta_bytes;
-  P->off_words = P->off_tables + align_up(table_off, kAlign);
-  P->ws_bytes = P->off_words + align_up((size_t)(word_off + kChunkWords) * 2, kAlign);
+  P->off_tables = align_up((size_t)(word_off + kChunkWords) * 2, kAlign);
+  P->off_meta = P->off_tables + align_up(table_off, kAlign);
+  P->ws_bytes = P->off_meta + meta_bytes;
 
   P->meta.assign(meta_bytes, 0);
   std::memcpy(P->meta.data() + P->off_streams, ds.data(), ds.size() * sizeof(DevStream));
@@ -251,20 +253,58 @@ static int cuda_fail(cudaError_t e, const char* what) {
   return fail(RECOIL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+namespace recoil {
+size_t plan_bulk_bytes(const recoil_plan* P) { return P->off_meta; }
+
+int plan_upload_parts(recoil_plan* P, void* d_ws, size_t ws_bytes, cudaStream_t cs, bool bulk, bool meta) {
+  if (!P || !d_ws) return fail(RECOIL_EINVAL, "null argument");
+  if (ws_bytes < P->ws_bytes) return fail(RECOIL_ENOMEM, "workspace too small");
+  if (((uintptr_t)d_ws) % kAlign) return fail(RECOIL_EINVAL, "workspace must be 256-byte aligned");
+  uint8_t* ws = (uint8_t*)d_ws;
+  if (P->sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+  }
+  cudaError_t e = cudaSuccess;
+  if (meta) e = cudaMemcpyAsync(ws + P->off_meta, P->meta.data(), P->meta.size(), cudaMemcpyHostToDevice, cs);
+  if (bulk) {
+    if (e == cudaSuccess && !P->tables.empty())
+      e = cudaMemcpyAsync(ws + P->off_tables, P->tables.data(), P->tables.size(), cudaMemcpyHostToDevice, cs);
+    for (size_t i = 0; e == cudaSuccess && i < P->streams.size(); i++) {
+      const Stream& s = *P->streams[i];
+      if (!s.n_words()) continue;
+      e = cudaMemcpyAsync(ws + P->word_off[i] * 2, s.word_data(), s.n_words() * 2, cudaMemcpyHostToDevice, cs);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "upload");
+  if (P->d_ws != ws && P->graph) {
+    cudaGraphExecDestroy(P->graph);
+    P->graph = nullptr;
+  }
+  P->d_ws = ws;
+  P->uploaded = true;
+  P->outs_on_device = false;
+  return RECOIL_OK;
+}
+}  // namespace recoil
+
 static int plan_launch(recoil_plan* P, cudaStream_t cs) {
   P->launches = 0;
-  DevControl* ctl = reinterpret_cast<DevControl*>(P->d_ws);
+  uint8_t* meta = P->d_ws + P->off_meta;
+  DevControl* ctl = reinterpret_cast<DevControl*>(meta);
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DevControl), cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   LaunchArgs a{};
-  a.streams = reinterpret_cast<const DevStream*>(P->d_ws + P->off_streams);
-  a.entries = reinterpret_cast<const DevEntry*>(P->d_ws + P->off_entries);
-  a.word_pool = reinterpret_cast<const uint16_t*>(P->d_ws + P->off_words);
+  a.streams = reinterpret_cast<const DevStream*>(meta + P->off_streams);
+  a.entries = reinterpret_cast<const DevEntry*>(meta + P->off_entries);
+  a.word_pool = reinterpret_cast<const uint16_t*>(P->d_ws);
   a.table_pool = P->d_ws + P->off_tables;
-  a.outs = reinterpret_cast<void* const*>(P->d_ws + P->off_outs);
+  a.outs = reinterpret_cast<void* const*>(meta + P->off_outs);
   a.control = ctl;
   a.warps = P->warps;
-  const DevItem* items = reinterpret_cast<const DevItem*>(P->d_ws + P->off_items);
+  const DevItem* items = reinterpret_cast<const DevItem*>(meta + P->off_items);
   if (P->opts.flags & RECOIL_BATCH_PER_STREAM) {
     for (size_t s = 0; s < P->streams.size(); s++) {
       if (!P->stream_item_count[s]) continue;
@@ -346,35 +386,7 @@ int recoil_plan_workspace_size(const recoil_plan* P, size_t* bytes) {
 
 int recoil_plan_upload(recoil_plan* P, void* d_ws, size_t ws_bytes, void* stream) {
   clear_error();
-  if (!P || !d_ws) return fail(RECOIL_EINVAL, "null argument");
-  if (ws_bytes < P->ws_bytes) return fail(RECOIL_ENOMEM, "workspace too small");
-  if (((uintptr_t)d_ws) % kAlign) return fail(RECOIL_EINVAL, "workspace must be 256-byte aligned");
-  cudaStream_t cs = (cudaStream_t)stream;
-  uint8_t* ws = (uint8_t*)d_ws;
-  if (P->sms == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "device query");
-  }
-  cudaError_t e = cudaMemcpyAsync(ws, P->meta.data(), P->meta.size(), cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess && !P->tables.empty())
-    e = cudaMemcpyAsync(ws + P->off_tables, P->tables.data(), P->tables.size(), cudaMemcpyHostToDevice, cs);
-  for (size_t i = 0; e == cudaSuccess && i < P->streams.size(); i++) {
-    const Stream& s = *P->streams[i];
-    if (!s.n_words()) continue;
-    e = cudaMemcpyAsync(ws + P->off_words + P->word_off[i] * 2, s.word_data(), s.n_words() * 2,
-                        cudaMemcpyHostToDevice, cs);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "upload");
-  if (P->d_ws != ws && P->graph) {
-    cudaGraphExecDestroy(P->graph);
-    P->graph = nullptr;
-  }
-  P->d_ws = ws;
-  P->uploaded = true;
-  P->outs_on_device = false;
-  return RECOIL_OK;
+  return plan_upload_parts(P, d_ws, ws_bytes, (cudaStream_t)stream, true, true);
 }
 
 int recoil_plan_decode(recoil_plan* P, void* const* d_outs, void* stream) {
@@ -389,7 +401,8 @@ int recoil_plan_decode(recoil_plan* P, void* const* d_outs, void* stream) {
     for (size_t i = 0; i < count; i++)
       if (!d_outs[i] && P->streams[i]->n_syms) return fail(RECOIL_EINVAL, "null output buffer");
     P->outs.assign(d_outs, d_outs + count);
-    cudaError_t e = cudaMemcpyAsync(P->d_ws + P->off_outs, P->outs.data(), count * 8, cudaMemcpyHostToDevice, cs);
+    cudaError_t e = cudaMemcpyAsync(P->d_ws + P->off_meta + P->off_outs, P->outs.data(), count * 8,
+                                    cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "output pointer upload");
     P->outs_on_device = true;
   }
@@ -421,7 +434,7 @@ int recoil_plan_errors(recoil_plan* P, void* stream, uint32_t* flags) {
   if (!P || !flags) return fail(RECOIL_EINVAL, "null argument");
   if (!P->uploaded) return fail(RECOIL_EINVAL, "plan not uploaded");
   DevControl c;
-  cudaError_t e = cudaMemcpyAsync(&c, P->d_ws, sizeof c, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  cudaError_t e = cudaMemcpyAsync(&c, P->d_ws + P->off_meta, sizeof c, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "error readback");
   *flags = c.errors;

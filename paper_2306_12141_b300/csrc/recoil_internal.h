@@ -148,6 +148,10 @@ struct PlanImage {
 struct recoil_plan;
 namespace recoil {
 void plan_image(const recoil_plan* plan, PlanImage* out);
+// Upload the bulk region (words, tables) and/or the descriptors of a plan.
+int plan_upload_parts(recoil_plan* plan, void* d_ws, size_t ws_bytes, cudaStream_t s, bool bulk, bool meta);
+// Bytes of the bulk region at the start of a plan's workspace.
+size_t plan_bulk_bytes(const recoil_plan* plan);
 
 // Error reporting (thread-local message).
 int fail(int code, const std::string& msg);

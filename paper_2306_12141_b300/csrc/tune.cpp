@@ -1,0 +1,193 @@
+// Autotuner for batched decoding: picks warps per CTA and the split size a
+// batch is combined to by timing each candidate on the caller's own streams.
+//
+// Candidates differ only in how streams are split, so they share the bulk of
+// the device image (words and tables): it is uploaded once and each candidate
+// uploads only its descriptors. Each candidate gets one warm-up decode and
+// `steps` timed decodes (CUDA events on the caller's stream); the median
+// decides. Results can be cached in a text file keyed by the GPU and the batch
+// shape, so a serving process tunes once.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <vector>
+
+#include "recoil_internal.h"
+
+namespace recoil {
+namespace {
+
+const uint32_t kWarps[] = {4, 8, 16};
+const uint32_t kSplit[] = {32768, 65536, 131072, 262144};
+
+std::string tune_key(const recoil_stream* const* s, uint32_t count) {
+  int dev = 0, sms = 0;
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof prop);
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaGetDeviceProperties(&prop, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  uint64_t total = 0;
+  uint32_t nmask = 0, bmask = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    total += s[i]->n_syms * s[i]->sym_bytes;
+    nmask |= 1u << (s[i]->n_bits & 31);
+    bmask |= s[i]->sym_bytes;
+  }
+  std::ostringstream k;
+  for (const char* c = prop.name; *c; c++) k << (*c == ' ' ? '_' : *c);
+  k << "|sm" << sms << "|c" << (count ? (int)std::log2((double)count) : 0) << "|b"
+    << (total ? (int)std::log2((double)total) : 0) << "|n" << nmask << "|s" << bmask;
+  return k.str();
+}
+
+bool cache_lookup(const char* path, const std::string& key, recoil_batch_opts* best, float* ms) {
+  if (!path) return false;
+  std::ifstream f(path);
+  std::string line;
+  bool hit = false;
+  while (std::getline(f, line)) {
+    std::istringstream in(line);
+    std::string k;
+    uint32_t w = 0, sp = 0;
+    float t = 0;
+    if (in >> k >> w >> sp >> t && k == key && warps_supported(w)) {
+      best->warps_per_cta = w;
+      best->split_symbols = sp;
+      *ms = t;
+      hit = true;                          // the last line for a key wins
+    }
+  }
+  return hit;
+}
+
+void cache_store(const char* path, const std::string& key, const recoil_batch_opts& b, float ms) {
+  if (!path) return;
+  std::ofstream f(path, std::ios::app);
+  f << key << ' ' << b.warps_per_cta << ' ' << b.split_symbols << ' ' << ms << '\n';
+}
+
+struct Candidate {
+  recoil_batch_opts opts;
+  recoil_plan* plan = nullptr;
+};
+
+}  // namespace
+}  // namespace recoil
+
+using namespace recoil;
+
+extern "C" {
+
+int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t count, size_t* bytes) {
+  clear_error();
+  if (!bytes) return fail(RECOIL_EINVAL, "null argument");
+  size_t mx = 0;
+  for (uint32_t w : kWarps)
+    for (uint32_t sp : kSplit) {
+      recoil_batch_opts o{w, 0, sp, 0};
+      size_t b = 0;
+      int rc = recoil_workspace_size(streams, count, &o, &b);
+      if (rc) return rc;
+      mx = std::max(mx, b);
+    }
+  *bytes = mx;
+  return RECOIL_OK;
+}
+
+int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* const* d_outs, void* d_ws,
+                    size_t ws_bytes, void* cuda_stream, const recoil_tune_opts* topts, recoil_batch_opts* best,
+                    float* best_ms) {
+  clear_error();
+  if (!best || (count && (!streams || !d_outs))) return fail(RECOIL_EINVAL, "null argument");
+  const uint32_t steps = topts && topts->steps ? topts->steps : 3;
+  const char* cache = topts ? topts->cache_path : nullptr;
+  const bool refresh = topts && (topts->flags & RECOIL_TUNE_REFRESH);
+  const std::string key = tune_key(streams, count);
+  float ms = 0;
+  recoil_batch_opts hit{};
+  if (!refresh && cache_lookup(cache, key, &hit, &ms)) {
+    *best = hit;
+    if (best_ms) *best_ms = ms;
+    return RECOIL_OK;
+  }
+  cudaStream_t cs = (cudaStream_t)cuda_stream;
+  std::vector<Candidate> cands;
+  auto cleanup = [&]() {
+    for (Candidate& c : cands) recoil_plan_free(c.plan);
+  };
+  size_t bulk = 0;
+  for (uint32_t w : kWarps)
+    for (uint32_t sp : kSplit) {
+      Candidate c;
+      c.opts = recoil_batch_opts{w, 0, sp, 0};
+      int rc = recoil_plan_create(streams, count, &c.opts, &c.plan);
+      if (rc) {
+        cleanup();
+        return rc;
+      }
+      size_t need = 0;
+      recoil_plan_workspace_size(c.plan, &need);
+      if (need > ws_bytes) {
+        recoil_plan_free(c.plan);
+        cleanup();
+        return fail(RECOIL_ENOMEM, "workspace too small for tuning (see recoil_autotune_workspace_size)");
+      }
+      if (cands.empty()) bulk = plan_bulk_bytes(c.plan);
+      if (plan_bulk_bytes(c.plan) != bulk) {
+        recoil_plan_free(c.plan);
+        cleanup();
+        return fail(RECOIL_EINVAL, "internal: candidates disagree on the bulk layout");
+      }
+      cands.push_back(c);
+    }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cleanup();
+    return fail(RECOIL_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+  }
+  int rc = RECOIL_OK;
+  float best_t = 0;
+  int best_i = -1;
+  for (size_t i = 0; i < cands.size() && !rc; i++) {
+    rc = plan_upload_parts(cands[i].plan, d_ws, ws_bytes, cs, i == 0, true);
+    if (!rc) rc = recoil_plan_decode(cands[i].plan, d_outs, cs);          // warm-up
+    std::vector<float> t;
+    for (uint32_t k = 0; k < steps && !rc; k++) {
+      cudaEventRecord(e0, cs);
+      rc = recoil_plan_decode(cands[i].plan, d_outs, cs);
+      cudaEventRecord(e1, cs);
+      if (!rc && (ce = cudaEventSynchronize(e1)) != cudaSuccess)
+        rc = fail(RECOIL_ECUDA, std::string("tuning: ") + cudaGetErrorString(ce));
+      float v = 0;
+      if (!rc) cudaEventElapsedTime(&v, e0, e1);
+      t.push_back(v);
+    }
+    if (rc) break;
+    uint32_t flags = 0;
+    rc = recoil_plan_errors(cands[i].plan, cuda_stream, &flags);
+    std::sort(t.begin(), t.end());
+    const float med = t[t.size() / 2];
+    if (!rc && (best_i < 0 || med < best_t)) {
+      best_t = med;
+      best_i = (int)i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc && best_i >= 0) {
+    *best = cands[best_i].opts;
+    if (best_ms) *best_ms = best_t;
+    cache_store(cache, key, *best, best_t);
+  }
+  cleanup();
+  return rc;
+}
+
+}  // extern "C"

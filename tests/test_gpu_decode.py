@@ -242,3 +242,24 @@ def zipf_1gib(recoil_lib):
     stream = recoil_lib.encode_with_splits(s, st.n_bits, 65536)
     assert stream.info["n_entries"] == 65536
     return torch.from_numpy(s).cuda(), stream, s
+
+
+def test_autotune_chooses_a_working_configuration(recoil_lib, tmp_path):
+    R = recoil_lib
+    syms, streams = _batch_streams(R, count=40, seed=44)
+    need = R.autotune_workspace_size(streams)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    outs = [torch.zeros(max(1, len(s) * s.itemsize), dtype=torch.uint8, device="cuda") for s in syms]
+    ptrs = [o.data_ptr() for o in outs]
+    cs = torch.cuda.current_stream()
+    cache = str(tmp_path / "tune.txt")
+    best, ms = R.autotune(streams, ptrs, ws, need, cs, steps=2, cache_path=cache)
+    assert best["warps_per_cta"] in (4, 8, 16) and best["split_symbols"] in (32768, 65536, 131072, 262144)
+    assert ms > 0
+    for s, o in zip(syms, outs):                               # the tuning decodes are exact too
+        assert np.array_equal(o.cpu().numpy()[: len(s) * s.itemsize].view(s.dtype), s)
+    again, ms2 = R.autotune(streams, ptrs, ws, need, cs, cache_path=cache)
+    assert again == best and abs(ms2 - ms) < 1e-3               # served from the cache
+    res = gpu_decode(R, streams, best)
+    for s, out in zip(syms, res):
+        assert np.array_equal(out, s)
