@@ -204,6 +204,65 @@ int recoil_decode_batch(const recoil_stream* const* streams, uint32_t count, voi
                         void* d_workspace, size_t ws_bytes, void* cuda_stream,
                         const recoil_batch_opts* opts);
 
+/* -------------------------------------------------------------- serving */
+
+typedef struct {
+  size_t budget_bytes;       /* device memory admitted requests' outputs may use at once (e.g. 20 GiB) */
+  uint32_t max_inflight;     /* launches on the device at once, each on its own CUDA stream (default 8) */
+  uint32_t max_batch;        /* requests admitted into one launch (default 64) */
+  uint32_t warps_per_cta;    /* default 8 (4 with RECOIL_SERVE_PER_REQUEST) */
+  uint32_t flags;            /* RECOIL_SERVE_* */
+  size_t meta_bytes;         /* descriptor area per launch (default 4 MiB) */
+  double timeout_s;          /* wall-clock limit of the run (default 60 s) */
+} recoil_serve_opts;
+
+#define RECOIL_SERVE_PER_REQUEST 1u  /* baseline: one launch per request with every encoded split, one at a time */
+
+typedef struct {
+  double arrival_s;          /* request arrival, seconds from the start of the run */
+  double admit_s;            /* when the loop admitted it */
+  double done_s;             /* device completion of the launch that carried it */
+  uint32_t splits;           /* split count it was decoded with */
+  uint32_t launch;           /* index of that launch */
+} recoil_request_result;
+
+typedef struct {
+  uint64_t requests;
+  uint64_t launches;
+  uint64_t symbol_bytes;     /* decoded bytes over all requests */
+  double makespan_s;         /* first arrival to last completion */
+  double decoded_gbs;        /* symbol_bytes / makespan */
+  double p50_ms, p99_ms, mean_ms;   /* latency = done - arrival */
+  uint32_t max_inflight;     /* most launches seen on the device at once */
+} recoil_serve_stats;
+
+/* Arena bytes recoil_serve needs: resident pool words and tables, one
+ * descriptor area per launch slot, and the output budget. */
+int recoil_serve_arena_size(const recoil_stream* const* pool, uint32_t pool_count, const recoil_serve_opts* opts,
+                            size_t* bytes);
+
+/*
+ * Serve decode requests with continuous batching on the current GPU (the
+ * content-delivery setting of Sec. 3.3: each request is combined to the
+ * parallelism the decoder has when it is admitted). The pool's words and
+ * tables are uploaded once into d_arena (resident). Request r asks for pool
+ * stream req_stream[r] at req_arrival_s[r] (seconds from the start, non-
+ * decreasing) and is replayed in real time. Arrived requests are admitted in
+ * order while the budget and a launch slot allow, combined to their share of
+ * the free warp slots, and launched together as one persistent decode on the
+ * slot's CUDA stream; launches overlap on the device. Outputs go to
+ * d_req_outs[r] (caller device buffers of n_syms * sym_bytes) or, with
+ * d_req_outs NULL, to arena memory that is reused once a request completes.
+ * results[r] receives the timeline of request r, *stats the summary (may be
+ * NULL). Returns when every request has completed. Errors: EINVAL, ENOMEM
+ * (arena or descriptor area too small), ECORRUPT, ETIMEOUT (timeout_s passed;
+ * the launches already made are finished first), ECUDA.
+ */
+int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const uint32_t* req_stream,
+                 const double* req_arrival_s, uint32_t n_req, void* d_arena, size_t arena_bytes,
+                 void* const* d_req_outs, const recoil_serve_opts* opts, recoil_request_result* results,
+                 recoil_serve_stats* stats);
+
 /* ----------------------------------------------------------- autotuning */
 
 typedef struct {

@@ -43,6 +43,26 @@ class BatchOpts(C.Structure):
                 ("split_symbols", C.c_uint32), ("flags", C.c_uint32)]
 
 
+class ServeOpts(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_inflight", C.c_uint32), ("max_batch", C.c_uint32),
+                ("warps_per_cta", C.c_uint32), ("flags", C.c_uint32), ("meta_bytes", C.c_size_t),
+                ("timeout_s", C.c_double)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("arrival_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("splits", C.c_uint32), ("launch", C.c_uint32)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("requests", C.c_uint64), ("launches", C.c_uint64), ("symbol_bytes", C.c_uint64),
+                ("makespan_s", C.c_double), ("decoded_gbs", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_inflight", C.c_uint32)]
+
+
+SERVE_PER_REQUEST = 1
+
+
 class TuneOpts(C.Structure):
     _fields_ = [("steps", C.c_uint32), ("flags", C.c_uint32), ("cache_path", C.c_char_p)]
 
@@ -55,7 +75,7 @@ EXPORTS = [
     "recoil_plan_create", "recoil_plan_workspace_size", "recoil_plan_upload", "recoil_plan_decode",
     "recoil_plan_errors", "recoil_plan_launches", "recoil_plan_free", "recoil_workspace_size",
     "recoil_decode", "recoil_decode_batch", "recoil_decode_noalloc", "recoil_autotune",
-    "recoil_autotune_workspace_size",
+    "recoil_autotune_workspace_size", "recoil_serve", "recoil_serve_arena_size",
 ]
 
 _lib = None
@@ -92,6 +112,9 @@ def lib():
         L.recoil_decode.argtypes = [vp, vp, vp, C.c_size_t, vp]
         L.recoil_decode_batch.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(BatchOpts)]
         L.recoil_decode_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
+        L.recoil_serve_arena_size.argtypes = [vp, u32, C.POINTER(ServeOpts), C.POINTER(C.c_size_t)]
+        L.recoil_serve.argtypes = [vp, u32, vp, vp, u32, vp, C.c_size_t, vp, C.POINTER(ServeOpts),
+                                   C.POINTER(RequestResult), C.POINTER(ServeStats)]
         L.recoil_autotune_workspace_size.argtypes = [vp, u32, C.POINTER(C.c_size_t)]
         L.recoil_autotune.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(TuneOpts),
                                       C.POINTER(BatchOpts), C.POINTER(C.c_float)]
@@ -345,6 +368,34 @@ def recoil_autotune(streams, outs, workspace, nbytes: int, cuda_stream=None, ste
     return {k: getattr(best, k) for k, _ in BatchOpts._fields_}, float(ms.value)
 
 
+def _serve_opts(budget_bytes, max_inflight=0, max_batch=0, warps_per_cta=0, per_request=False, meta_bytes=0,
+                timeout_s=0.0):
+    return ServeOpts(int(budget_bytes), max_inflight, max_batch, warps_per_cta,
+                     SERVE_PER_REQUEST if per_request else 0, meta_bytes, timeout_s)
+
+
+def recoil_serve_arena_size(pool, budget_bytes, **kw) -> int:
+    o = _serve_opts(budget_bytes, **kw)
+    n = C.c_size_t()
+    _check(lib().recoil_serve_arena_size(_handles(pool), len(pool), C.byref(o), C.byref(n)))
+    return n.value
+
+
+def recoil_serve(pool, req_stream, req_arrival_s, arena, arena_bytes: int, budget_bytes: int, outs=None, **kw):
+    """Continuous-batching serving run. Returns (per-request results as a dict of arrays, stats dict)."""
+    o = _serve_opts(budget_bytes, **kw)
+    rs = np.ascontiguousarray(req_stream, dtype=np.uint32)
+    ra = np.ascontiguousarray(req_arrival_s, dtype=np.float64)
+    n = len(rs)
+    res = (RequestResult * max(1, n))()
+    st = ServeStats()
+    optr = _ptr_array(outs) if outs is not None else None
+    _check(lib().recoil_serve(_handles(pool), len(pool), _ptr(rs), _ptr(ra), n, _ptr(arena), arena_bytes, optr,
+                              C.byref(o), res, C.byref(st)))
+    out = {k: np.array([getattr(res[i], k) for i in range(n)]) for k, _ in RequestResult._fields_}
+    return out, {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+
 NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
@@ -371,4 +422,6 @@ decode = recoil_decode
 decode_batch = recoil_decode_batch
 decode_noalloc = recoil_decode_noalloc
 autotune = recoil_autotune
+serve = recoil_serve
+serve_arena_size = recoil_serve_arena_size
 autotune_workspace_size = recoil_autotune_workspace_size

@@ -62,6 +62,8 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
   return s.table_img;
 }
 
+}  // namespace
+
 // Device entries of a stream: kept regular entries in order, then the final one.
 void build_entries(const Stream& s, std::vector<DevEntry>& out) {
   const uint32_t N = (uint32_t)s.n_syms;
@@ -101,7 +103,6 @@ void build_entries(const Stream& s, std::vector<DevEntry>& out) {
   out.push_back(d);
 }
 
-}  // namespace
 }  // namespace recoil
 
 using namespace recoil;
@@ -240,6 +241,7 @@ void plan_image(const recoil_plan* P, PlanImage* o) {
   o->off_entries = P->off_entries;
   o->tables = P->tables.data();
   o->table_bytes = P->tables.size();
+  o->ws_off_tables = P->off_tables;
   o->warps = P->warps;
   for (uint32_t k = 0; k < kKinds; k++) {
     o->kind_first[k] = P->kind_first[k];
@@ -258,7 +260,7 @@ size_t plan_bulk_bytes(const recoil_plan* P) { return P->off_meta; }
 
 int plan_upload_parts(recoil_plan* P, void* d_ws, size_t ws_bytes, cudaStream_t cs, bool bulk, bool meta) {
   if (!P || !d_ws) return fail(RECOIL_EINVAL, "null argument");
-  if (ws_bytes < P->ws_bytes) return fail(RECOIL_ENOMEM, "workspace too small");
+  if (ws_bytes < (meta ? P->ws_bytes : P->off_meta)) return fail(RECOIL_ENOMEM, "workspace too small");
   if (((uintptr_t)d_ws) % kAlign) return fail(RECOIL_EINVAL, "workspace must be 256-byte aligned");
   uint8_t* ws = (uint8_t*)d_ws;
   if (P->sms == 0) {

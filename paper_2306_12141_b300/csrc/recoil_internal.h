@@ -141,6 +141,7 @@ struct PlanImage {
   size_t off_outs, off_streams, off_items, off_entries;
   const uint8_t* tables;
   size_t table_bytes;
+  size_t ws_off_tables;      // workspace offset of the tables (words start at 0)
   uint32_t warps;
   uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds];
 };
@@ -148,6 +149,8 @@ struct PlanImage {
 struct recoil_plan;
 namespace recoil {
 void plan_image(const recoil_plan* plan, PlanImage* out);
+// Device entries of a stream's kept splits, the final-state entry last (plan.cpp).
+void build_entries(const Stream& s, std::vector<DevEntry>& out);
 // Upload the bulk region (words, tables) and/or the descriptors of a plan.
 int plan_upload_parts(recoil_plan* plan, void* d_ws, size_t ws_bytes, cudaStream_t s, bool bulk, bool meta);
 // Bytes of the bulk region at the start of a plan's workspace.
