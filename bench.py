@@ -55,11 +55,14 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="batch", choices=["batch", "zipf"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "zipf", "serve"])
     ap.add_argument("--splits", type=int, default=9472, help="zipf: decoder split count")
     ap.add_argument("--sweep", type=lambda v: [int(x) for x in v.split(",") if x], default=[148, 592, 2368, 9472],
                     help="zipf: split counts to sweep (empty to skip)")
     ap.add_argument("--soak", type=float, default=1.0, help="seconds of untimed steps while sampling clocks")
+    ap.add_argument("--serve-rate", type=float, default=10000.0, help="batch: serving check at this request rate")
+    ap.add_argument("--e2e-groups", type=int, default=8, help="stream groups of the end-to-end pipeline")
+    ap.add_argument("--serve-requests", type=int, default=5000, help="batch: requests in the serving check (0: skip)")
     return ap.parse_args()
 
 
@@ -214,6 +217,30 @@ ZIPF_WORKLOAD = ("single stream: 1 GiB of Zipf(s=1.2) bytes over 256 symbols, n=
                  "splits and combined to the decoder's split count")
 
 
+SERVE_RATES = [2000, 5000, 10000, 20000, 50000]
+
+
+def serving(R, torch, dev, pool, rate, n_req, budget, arena, per_request):
+    """One serving run over the pool at a Poisson rate; latency and throughput summary."""
+    picks = workloads.request_picks(len(pool), n_req, seed=7)
+    arrive = workloads.poisson_arrivals(float(rate), n_req, seed=7)
+    res, st = R.serve(pool, picks, arrive, arena, arena.numel(), budget, per_request=per_request,
+                      timeout_s=300.0)
+    return {"p50_ms": round(st["p50_ms"], 4), "p99_ms": round(st["p99_ms"], 4), "mean_ms": round(st["mean_ms"], 4),
+            "decoded_gbs": round(st["decoded_gbs"], 2), "launches": st["launches"],
+            "max_inflight": st["max_inflight"], "mean_splits": round(float(np.mean(res["splits"])), 1)}
+
+
+def serving_block(R, torch, dev, pool, rates, n_req, budget=20 << 30):
+    arena = torch.empty(R.serve_arena_size(pool, budget), dtype=torch.uint8, device=dev)
+    out = {}
+    for rate in rates:
+        out[str(rate)] = {"recoil": serving(R, torch, dev, pool, rate, n_req, budget, arena, False),
+                          "per_request": serving(R, torch, dev, pool, rate, n_req, budget, arena, True)}
+    del arena
+    return out
+
+
 def make_workload(a, R, rank):
     """(description, specs, symbols, encoded streams, streams to decode) of the chosen workload."""
     if a.workload == "batch":
@@ -334,27 +361,37 @@ def run_ours(a):
             exact()
             extra["split_sweep_gbs"] = sweep
 
+        if batch and a.serve_requests > 0:
+            # continuous-batching serving over the same pool (Poisson arrivals, 20 GiB budget)
+            extra["serving"] = {"requests": a.serve_requests, "budget_gib": 20,
+                                "rates_hz": serving_block(R, torch, dev, streams, [a.serve_rate], a.serve_requests)}
+
         e2e = None
         if not a.no_e2e:
+            # end to end through the public API: the pipeline copies the words in from
+            # page-locked host memory, decodes and copies the symbols back, every step
             for st in streams:
                 R.stream_pin(st)
-            ep = R.Plan(streams, {k: v for k, v in opts.items() if k != "flags"})
-            host_out = torch.empty(out_bytes, dtype=torch.uint8, pin_memory=True)
+            pipe = R.Pipeline(streams, {k: v for k, v in opts.items() if k != "flags"}, groups=a.e2e_groups)
+            wsb, stb = pipe.sizes
+            pws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            stage = torch.empty(stb, dtype=torch.uint8, device=dev)
+            host = torch.empty(out_bytes + 256 * len(syms), dtype=torch.uint8, pin_memory=True)
             offs = np.concatenate([[0], np.cumsum([max(1, len(s) * s.itemsize) for s in syms])])
-            flat = torch.empty(int(offs[-1]), dtype=torch.uint8, device=dev)
-            flat_ptrs = [flat.data_ptr() + int(o) for o in offs[:-1]]
-
-            def e2e_step():
-                ep.upload(ws, stream=cs)
-                ep.decode(flat_ptrs, cs)
-                host_out.copy_(flat[:out_bytes], non_blocking=True)
-
-            e_ms = timed(e2e_step, max(2, a.steps // 2), 1)
-            assert ep.errors(cs) == 0
+            host_ptrs = [host.data_ptr() + int(o) for o in offs[:-1]]
+            e_ms = timed(lambda: pipe.run(host_ptrs, pws, wsb, stage, stb, cs), max(3, a.steps // 2), 1)
+            assert pipe.errors() == 0
+            hv = host.numpy()
+            bad = sum(1 for s, o in zip(syms, offs[:-1]) if not np.array_equal(hv[int(o): int(o) + len(s) * s.itemsize],
+                                                                                s.view(np.uint8)))
+            assert bad == 0, f"{bad} streams wrong end to end"
+            h2d = sum(2 * st.info["n_words"] for st in streams)
             e2e = {"value": world * out_bytes / (statistics.mean(e_ms) * 1e-3) / 1e9, "unit": "GB/s",
-                   "h2d_bytes_per_step": int(ep.workspace_size), "d2h_bytes_per_step": int(out_bytes),
-                   "ms_per_step": statistics.mean(e_ms)}
-            del flat
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_bytes),
+                   "ms_per_step": statistics.mean(e_ms), "groups": a.e2e_groups,
+                   "note": "recoil_pipeline_run: H2D of words (+ descriptors, tables), decode, D2H of the symbols, "
+                           "overlapped across stream groups"}
+            del pws, stage
 
     mean_ms = statistics.mean(ms)
     if dist:
@@ -395,9 +432,34 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(a):
+    """--workload serve: the serving sweep (rates 2k-50k/s, 20000 requests each) over the batch pool."""
+    import torch
+    import paper_2306_12141_b300 as R
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    specs, syms, streams = build_batch(R, a.streams, a.scale)
+    n_req = a.serve_requests if a.serve_requests > 0 else 20000
+    with Clocks(dev.index) as clk:
+        sweep = serving_block(R, torch, dev, streams, SERVE_RATES, n_req)
+    top = sweep[str(SERVE_RATES[-1])]
+    line = {"metric": METRIC, "value": top["recoil"]["decoded_gbs"], "unit": "GB/s", "n_gpus": 1,
+            "steps": len(SERVE_RATES), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals over the " + BATCH_WORKLOAD + ", 20 GiB budget",
+                       "requests_per_rate": n_req},
+            "latency": {r: {"p50_ms": v["recoil"]["p50_ms"], "p99_ms": v["recoil"]["p99_ms"]} for r, v in sweep.items()},
+            "serving": sweep, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        if args.serve_requests == 5000:
+            args.serve_requests = 20000
+        run_serve(args)
     else:
         run_ours(args)

@@ -204,6 +204,42 @@ int recoil_decode_batch(const recoil_stream* const* streams, uint32_t count, voi
                         void* d_workspace, size_t ws_bytes, void* cuda_stream,
                         const recoil_batch_opts* opts);
 
+/* ------------------------------------------------- host-to-host pipeline */
+
+typedef struct recoil_pipeline recoil_pipeline;   /* opaque: grouped plans + copy/compute streams */
+
+/*
+ * Prepare host-to-host decoding of `count` streams with copy/compute overlap:
+ * the streams are cut into `groups` (0 = 8) groups of about equal output
+ * bytes, each with its own plan (opts as for recoil_plan_create) and page-
+ * locked copies of its descriptors and tables. For full link speed pin the
+ * streams' words first (recoil_stream_pin). The streams must outlive the
+ * pipeline. Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int recoil_pipeline_create(const recoil_stream* const* streams, uint32_t count, const recoil_batch_opts* opts,
+                           uint32_t groups, recoil_pipeline** out);
+
+/* Device bytes a run needs: the workspace and the staging buffer for the symbols. */
+int recoil_pipeline_sizes(const recoil_pipeline* p, size_t* ws_bytes, size_t* staging_bytes);
+
+/*
+ * Decode every stream into host memory: h_outs[i] receives n_syms * sym_bytes
+ * bytes (page-locked for full link speed). Per group, on three internal CUDA
+ * streams: copy the group in, decode it, copy its symbols out, so copies in
+ * both directions overlap the decoding of other groups. The run starts after
+ * work already queued on cuda_stream and cuda_stream waits for its end, so
+ * synchronising cuda_stream (or an event recorded on it) ends the run.
+ * d_ws and d_staging: caller device buffers of at least the sizes above,
+ * 256-byte aligned. Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int recoil_pipeline_run(recoil_pipeline* p, void* const* h_outs, void* d_ws, size_t ws_bytes, void* d_staging,
+                        size_t staging_bytes, void* cuda_stream);
+
+/* After a run has finished: error flags of its decodes (ECORRUPT if any). */
+int recoil_pipeline_errors(recoil_pipeline* p, uint32_t* flags);
+
+void recoil_pipeline_free(recoil_pipeline* p);
+
 /* -------------------------------------------------------------- serving */
 
 typedef struct {

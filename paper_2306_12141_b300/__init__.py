@@ -76,6 +76,8 @@ EXPORTS = [
     "recoil_plan_errors", "recoil_plan_launches", "recoil_plan_free", "recoil_workspace_size",
     "recoil_decode", "recoil_decode_batch", "recoil_decode_noalloc", "recoil_autotune",
     "recoil_autotune_workspace_size", "recoil_serve", "recoil_serve_arena_size",
+    "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
+    "recoil_pipeline_free",
 ]
 
 _lib = None
@@ -112,6 +114,12 @@ def lib():
         L.recoil_decode.argtypes = [vp, vp, vp, C.c_size_t, vp]
         L.recoil_decode_batch.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(BatchOpts)]
         L.recoil_decode_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
+        L.recoil_pipeline_create.argtypes = [vp, u32, C.POINTER(BatchOpts), u32, pp]
+        L.recoil_pipeline_sizes.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        L.recoil_pipeline_run.argtypes = [vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp]
+        L.recoil_pipeline_errors.argtypes = [vp, C.POINTER(u32)]
+        L.recoil_pipeline_free.argtypes = [vp]
+        L.recoil_pipeline_free.restype = None
         L.recoil_serve_arena_size.argtypes = [vp, u32, C.POINTER(ServeOpts), C.POINTER(C.c_size_t)]
         L.recoil_serve.argtypes = [vp, u32, vp, vp, u32, vp, C.c_size_t, vp, C.POINTER(ServeOpts),
                                    C.POINTER(RequestResult), C.POINTER(ServeStats)]
@@ -366,6 +374,63 @@ def recoil_autotune(streams, outs, workspace, nbytes: int, cuda_stream=None, ste
     _check(lib().recoil_autotune(_handles(streams), len(streams), _ptr_array(outs), _ptr(workspace), nbytes,
                                  _stream_handle(cuda_stream), C.byref(t), C.byref(best), C.byref(ms)))
     return {k: getattr(best, k) for k, _ in BatchOpts._fields_}, float(ms.value)
+
+
+class Pipeline:
+    """Host-to-host decoding of a batch with copy/compute overlap (recoil_pipeline_*)."""
+
+    def __init__(self, streams, opts=None, groups: int = 8):
+        self.streams = list(streams)
+        h = C.c_void_p()
+        o = _opts(opts)
+        _check(lib().recoil_pipeline_create(_handles(self.streams), len(self.streams),
+                                            C.byref(o) if o is not None else None, groups, C.byref(h)))
+        self.handle = h.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.recoil_pipeline_free(self.handle)
+            self.handle = None
+
+    @property
+    def sizes(self) -> tuple[int, int]:
+        a, b = C.c_size_t(), C.c_size_t()
+        _check(lib().recoil_pipeline_sizes(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def run(self, host_outs, workspace, ws_bytes: int, staging, staging_bytes: int, stream=None) -> None:
+        self._outs = _ptr_array(host_outs)
+        _check(lib().recoil_pipeline_run(self.handle, self._outs, _ptr(workspace), ws_bytes, _ptr(staging),
+                                         staging_bytes, _stream_handle(stream)))
+
+    def errors(self) -> int:
+        f = C.c_uint32()
+        rc = lib().recoil_pipeline_errors(self.handle, C.byref(f))
+        if rc not in (OK, ECORRUPT):
+            _check(rc)
+        return f.value
+
+
+def recoil_pipeline_create(streams, opts=None, groups: int = 8) -> Pipeline:
+    return Pipeline(streams, opts, groups)
+
+
+def recoil_pipeline_sizes(p: Pipeline) -> tuple[int, int]:
+    return p.sizes
+
+
+def recoil_pipeline_run(p: Pipeline, host_outs, workspace, ws_bytes, staging, staging_bytes, stream=None):
+    p.run(host_outs, workspace, ws_bytes, staging, staging_bytes, stream)
+
+
+def recoil_pipeline_errors(p: Pipeline) -> int:
+    return p.errors()
+
+
+def recoil_pipeline_free(p: Pipeline) -> None:
+    if p.handle:
+        lib().recoil_pipeline_free(p.handle)
+        p.handle = None
 
 
 def _serve_opts(budget_bytes, max_inflight=0, max_batch=0, warps_per_cta=0, per_request=False, meta_bytes=0,

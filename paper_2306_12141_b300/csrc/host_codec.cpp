@@ -49,10 +49,6 @@ int fail(int code, const std::string& msg) {
 
 void clear_error() { g_last_error.clear(); }
 
-Stream::~Stream() {
-  if (pinned_words) cudaFreeHost(const_cast<uint16_t*>(pinned_words));
-}
-
 bool Stream::constant() const {
   for (uint32_t f : freq)
     if (f == (1u << n_bits)) return true;
@@ -307,6 +303,7 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_strea
     s->n_syms = in->n_syms;
     s->freq = in->freq;
     s->words = in->words;
+    s->pinned_words = in->pinned_words;
     std::memcpy(s->final_x, in->final_x, sizeof s->final_x);
     const uint64_t K = in->entries.size() + 1;
     const uint64_t Mp = std::min<uint64_t>(target, K);
@@ -425,7 +422,9 @@ int recoil_stream_pin(recoil_stream* s) {
   cudaError_t e = cudaHostAlloc(&p, s->n_words() * 2, cudaHostAllocPortable);
   if (e != cudaSuccess) return fail(RECOIL_ECUDA, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
   std::memcpy(p, s->words->data(), s->n_words() * 2);
-  s->pinned_words = (const uint16_t*)p;
+  s->pinned_words = std::shared_ptr<const uint16_t>((const uint16_t*)p, [](const uint16_t* q) {
+    cudaFreeHost(const_cast<uint16_t*>(q));
+  });
   return RECOIL_OK;
 }
 

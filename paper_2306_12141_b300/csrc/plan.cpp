@@ -257,6 +257,8 @@ static int cuda_fail(cudaError_t e, const char* what) {
 
 namespace recoil {
 size_t plan_bulk_bytes(const recoil_plan* P) { return P->off_meta; }
+const std::vector<const Stream*>& plan_streams(const recoil_plan* P) { return P->streams; }
+const std::vector<uint64_t>& plan_word_offsets(const recoil_plan* P) { return P->word_off; }
 
 int plan_upload_parts(recoil_plan* P, void* d_ws, size_t ws_bytes, cudaStream_t cs, bool bulk, bool meta) {
   if (!P || !d_ws) return fail(RECOIL_EINVAL, "null argument");

@@ -46,7 +46,7 @@ struct Stream {
   uint64_t n_syms = 0;
   std::vector<uint32_t> freq;                      // quantised PDF f over the alphabet
   std::shared_ptr<const std::vector<uint16_t>> words;
-  const uint16_t* pinned_words = nullptr;          // optional page-locked copy of the words
+  std::shared_ptr<const uint16_t> pinned_words;    // optional page-locked copy, shared with combined streams
   uint32_t final_x[kW] = {};
   std::vector<Entry> entries;                      // regular entries, increasing word; final is implicit
 
@@ -55,9 +55,8 @@ struct Stream {
   mutable std::vector<uint8_t> table_img;          // decoder tables, padded to 16 B
   mutable uint32_t table_kind = 0;
 
-  ~Stream();
   uint64_t n_words() const { return words ? words->size() : 0; }
-  const uint16_t* word_data() const { return pinned_words ? pinned_words : (words ? words->data() : nullptr); }
+  const uint16_t* word_data() const { return pinned_words ? pinned_words.get() : (words ? words->data() : nullptr); }
   uint32_t alphabet() const { return (uint32_t)freq.size(); }
   bool constant() const;                           // a single symbol owns all 2^n slots
 };
@@ -155,6 +154,9 @@ void build_entries(const Stream& s, std::vector<DevEntry>& out);
 int plan_upload_parts(recoil_plan* plan, void* d_ws, size_t ws_bytes, cudaStream_t s, bool bulk, bool meta);
 // Bytes of the bulk region at the start of a plan's workspace.
 size_t plan_bulk_bytes(const recoil_plan* plan);
+// The streams a plan decodes (after combining) and their word offsets (in words).
+const std::vector<const Stream*>& plan_streams(const recoil_plan* plan);
+const std::vector<uint64_t>& plan_word_offsets(const recoil_plan* plan);
 
 // Error reporting (thread-local message).
 int fail(int code, const std::string& msg);

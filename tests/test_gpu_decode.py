@@ -263,3 +263,23 @@ def test_autotune_chooses_a_working_configuration(recoil_lib, tmp_path):
     res = gpu_decode(R, streams, best)
     for s, out in zip(syms, res):
         assert np.array_equal(out, s)
+
+
+def test_pipeline_decodes_host_to_host(recoil_lib):
+    R = recoil_lib
+    syms, streams = _batch_streams(R, count=50, seed=45)
+    for st in streams:
+        R.stream_pin(st)
+    pipe = R.Pipeline(streams, {"warps_per_cta": 8, "split_symbols": 32768}, groups=5)
+    wsb, stb = pipe.sizes
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.Stream()
+    for rep in range(2):
+        stage = torch.empty(stb + 256 * rep, dtype=torch.uint8, device="cuda")[256 * rep:]
+        host = [torch.full((max(1, len(s) * s.itemsize),), 0xAB, dtype=torch.uint8, pin_memory=True) for s in syms]
+        pipe.run([h.data_ptr() for h in host], ws, wsb, stage, stb, cs)
+        pipe.run([h.data_ptr() for h in host], ws, wsb, stage, stb, cs)      # back to back
+        cs.synchronize()
+        assert pipe.errors() == 0
+        for s, h in zip(syms, host):
+            assert np.array_equal(h.numpy()[: len(s) * s.itemsize].view(s.dtype), s)
