@@ -116,6 +116,28 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def recorded_traffic(key: str):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel sources still match it."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "decode_kernel_traffic.md")
+    src = os.path.join(ROOT, "paper_2306_12141_b300", "csrc")
+    try:
+        text = open(path).read()
+        h = hashlib.sha256()
+        for f in ("decode_kernels.cu", "recoil_internal.h"):
+            h.update(open(os.path.join(src, f), "rb").read())
+    except OSError:
+        return None
+    want = f"kernel_sources_sha256_16: {h.hexdigest()[:16]}"
+    if want not in text:
+        return None
+    for line in text.splitlines():
+        line = line.strip()
+        if line.startswith(f"traffic_bytes {key}:"):
+            return int(line.split(":")[1])
+    return None
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -401,6 +423,9 @@ def run_ours(a):
     value = world * out_bytes / (mean_ms * 1e-3) / 1e9
     peaks = measured_peaks()
     achieved = (out_bytes + in_bytes) / (mean_ms * 1e-3) / 1e9
+    tkey = (f"batch w{opts['warps_per_cta']} s{split_symbols}" if batch
+            else f"zipf w{opts['warps_per_cta']} k{a.splits}")
+    traffic = recorded_traffic(tkey) if a.scale == 1.0 and a.streams == workloads.BATCH_STREAMS else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
@@ -412,7 +437,7 @@ def run_ours(a):
                    "parallelism": f"weak x{world}", "l2": "inputs larger than L2 (no flush)",
                    "scale": a.scale},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"],
                      "kernel": "decode_kernel<kPacked8>", "bytes": "compressed words in + symbols out"},
         "clocks": clocks,
         "gpu_launches": launches * a.steps,

@@ -283,3 +283,27 @@ def test_pipeline_decodes_host_to_host(recoil_lib):
         assert pipe.errors() == 0
         for s, h in zip(syms, host):
             assert np.array_equal(h.numpy()[: len(s) * s.itemsize].view(s.dtype), s)
+
+
+@pytest.mark.parametrize("make", [workloads.skewed_256mib, workloads.uniform_256mib, workloads.gauss16_256mib],
+                         ids=["skewed", "uniform", "gauss16"])
+def test_distribution_extremes_full_size(recoil_lib, make):
+    """256 MiB each: P(0) = 0.95 (long synchronisation sections), uniform bytes, uint16 Gaussian at n = 15."""
+    R = recoil_lib
+    st = make()
+    s = st.symbols()
+    enc = R.encode_with_splits(s, st.n_bits, max(1, len(s) // 4096 // 4))
+    info = enc.info
+    if st.dist == "uniform":
+        assert abs(info["n_words"] - len(s) // 2) <= 2 * 32       # 8 bits per symbol exactly
+    ref = torch.from_numpy(s.view(np.uint8)).cuda()
+    for target in (9472, 148 * 48):
+        c = R.combine_splits(enc, target)
+        plan = R.Plan([c], {"warps_per_cta": 16})
+        ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device="cuda")
+        out = torch.empty(len(s) * s.itemsize, dtype=torch.uint8, device="cuda")
+        cs = torch.cuda.current_stream()
+        plan.upload(ws, stream=cs)
+        plan.decode([out.data_ptr()], cs)
+        assert plan.errors(cs) == 0
+        assert torch.equal(out, ref)
