@@ -116,6 +116,19 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def aggregate(ms_local: float, bytes_local: int, device=None):
+    """Job time = slowest rank; job bytes = all ranks' symbols (one rank: unchanged)."""
+    import torch
+    import torch.distributed as td
+    if device is None or not td.is_initialized() or td.get_world_size() == 1:
+        return ms_local, bytes_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    b = torch.tensor([float(bytes_local)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    td.all_reduce(b, op=td.ReduceOp.SUM)
+    return float(t.item()), int(b.item())
+
+
 def recorded_traffic(key: str):
     """DRAM bytes per launch recorded by an ncu capture, if the kernel sources still match it."""
     import hashlib
@@ -415,12 +428,8 @@ def run_ours(a):
                            "overlapped across stream groups"}
             del pws, stage
 
-    mean_ms = statistics.mean(ms)
-    if dist:
-        t = torch.tensor([mean_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        mean_ms = float(t.item())
-    value = world * out_bytes / (mean_ms * 1e-3) / 1e9
+    mean_ms, total_bytes = aggregate(statistics.mean(ms), out_bytes, dev if dist else None)
+    value = total_bytes / (mean_ms * 1e-3) / 1e9
     peaks = measured_peaks()
     achieved = (out_bytes + in_bytes) / (mean_ms * 1e-3) / 1e9
     tkey = (f"batch w{opts['warps_per_cta']} s{split_symbols}" if batch

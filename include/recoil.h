@@ -183,6 +183,15 @@ uint32_t recoil_plan_launches(const recoil_plan* plan);
 
 void recoil_plan_free(recoil_plan* plan);
 
+/*
+ * Assign streams to `world` ranks (one GPU each) for decoding a batch on
+ * several GPUs: longest first (by symbol bytes) to the least-loaded rank,
+ * ties to the lower rank. Streams decode independently, so the shards need
+ * no exchange while decoding. rank_of[i] receives stream i's rank.
+ * Host only. Errors: EINVAL.
+ */
+int recoil_shard(const recoil_stream* const* streams, uint32_t count, uint32_t world, uint32_t* rank_of);
+
 /* Workspace bytes recoil_decode_batch needs for these streams and options. */
 int recoil_workspace_size(const recoil_stream* const* streams, uint32_t count,
                           const recoil_batch_opts* opts, size_t* bytes);

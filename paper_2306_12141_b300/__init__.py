@@ -77,7 +77,7 @@ EXPORTS = [
     "recoil_decode", "recoil_decode_batch", "recoil_decode_noalloc", "recoil_autotune",
     "recoil_autotune_workspace_size", "recoil_serve", "recoil_serve_arena_size",
     "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
-    "recoil_pipeline_free",
+    "recoil_pipeline_free", "recoil_shard",
 ]
 
 _lib = None
@@ -114,6 +114,7 @@ def lib():
         L.recoil_decode.argtypes = [vp, vp, vp, C.c_size_t, vp]
         L.recoil_decode_batch.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(BatchOpts)]
         L.recoil_decode_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
+        L.recoil_shard.argtypes = [vp, u32, u32, vp]
         L.recoil_pipeline_create.argtypes = [vp, u32, C.POINTER(BatchOpts), u32, pp]
         L.recoil_pipeline_sizes.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         L.recoil_pipeline_run.argtypes = [vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp]
@@ -312,6 +313,13 @@ def recoil_workspace_size(streams, opts=None) -> int:
     return n.value
 
 
+def recoil_shard(streams, world: int) -> np.ndarray:
+    """Rank of each stream when a batch is split over `world` GPUs (longest first)."""
+    out = np.zeros(max(1, len(streams)), dtype=np.uint32)
+    _check(lib().recoil_shard(_handles(streams), len(streams), world, _ptr(out)))
+    return out[: len(streams)]
+
+
 def recoil_decode(stream: Stream, out, workspace, nbytes: int, cuda_stream=None) -> None:
     _check(lib().recoil_decode(stream.handle, _ptr(out), _ptr(workspace), nbytes, _stream_handle(cuda_stream)))
 
@@ -485,6 +493,7 @@ stream_pin = recoil_stream_pin
 workspace_size = recoil_workspace_size
 decode = recoil_decode
 decode_batch = recoil_decode_batch
+shard = recoil_shard
 decode_noalloc = recoil_decode_noalloc
 autotune = recoil_autotune
 serve = recoil_serve

@@ -476,6 +476,27 @@ int recoil_decode_batch(const recoil_stream* const* streams, uint32_t count, voi
   return rc;
 }
 
+int recoil_shard(const recoil_stream* const* streams, uint32_t count, uint32_t world, uint32_t* rank_of) {
+  clear_error();
+  if (!rank_of || world < 1 || (count && !streams)) return fail(RECOIL_EINVAL, "null argument or world < 1");
+  std::vector<uint32_t> order(count);
+  for (uint32_t i = 0; i < count; i++) {
+    if (!streams[i]) return fail(RECOIL_EINVAL, "null stream");
+    order[i] = i;
+  }
+  auto bytes = [&](uint32_t i) { return streams[i]->n_syms * streams[i]->sym_bytes; };
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return bytes(a) > bytes(b); });
+  std::vector<uint64_t> load(world, 0);
+  for (uint32_t i : order) {
+    uint32_t r = 0;
+    for (uint32_t k = 1; k < world; k++)
+      if (load[k] < load[r]) r = k;
+    rank_of[i] = r;
+    load[r] += bytes(i);
+  }
+  return RECOIL_OK;
+}
+
 int recoil_decode(const recoil_stream* s, void* d_out, void* d_ws, size_t ws_bytes, void* stream) {
   const recoil_stream* ss[1] = {s};
   void* outs[1] = {d_out};
