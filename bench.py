@@ -55,7 +55,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="batch", choices=["batch", "zipf", "serve"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "single", "zipf", "serve"])
+    ap.add_argument("--dist", default="zipf", choices=["zipf", "skewed", "uniform", "gauss16", "laplace"],
+                    help="single: which stream (zipf 1 GiB, the 256 MiB extremes, laplace 1 MiB)")
     ap.add_argument("--splits", type=int, default=9472, help="zipf: decoder split count")
     ap.add_argument("--sweep", type=lambda v: [int(x) for x in v.split(",") if x], default=[148, 592, 2368, 9472],
                     help="zipf: split counts to sweep (empty to skip)")
@@ -248,8 +250,13 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------- our arm
-ZIPF_WORKLOAD = ("single stream: 1 GiB of Zipf(s=1.2) bytes over 256 symbols, n=12, W=32, encoded at 65536 "
-                 "splits and combined to the decoder's split count")
+SINGLE = {
+    "zipf": (workloads.zipf_1gib, 1 << 30, "1 GiB of Zipf(s=1.2) bytes over 256 symbols, n=12"),
+    "skewed": (workloads.skewed_256mib, 1 << 28, "256 MiB of bytes with P(0)=0.95, the rest uniform, n=12"),
+    "uniform": (workloads.uniform_256mib, 1 << 28, "256 MiB of uniform bytes, n=12"),
+    "gauss16": (workloads.gauss16_256mib, 1 << 27, "2^27 uint16 symbols, Normal(2048, 200) clipped to 0..4095, n=15"),
+    "laplace": (workloads.laplace_1mib, 1 << 20, "1 MiB of Laplace(128, 8) bytes, n=11"),
+}
 
 
 SERVE_RATES = [2000, 5000, 10000, 20000, 50000]
@@ -281,10 +288,14 @@ def make_workload(a, R, rank):
     if a.workload == "batch":
         specs, syms, streams = build_batch(R, a.streams, a.scale, rank)
         return BATCH_WORKLOAD, specs, syms, streams, streams
-    st = workloads.zipf_1gib(int((1 << 30) * a.scale))
+    make, n_full, what = SINGLE[a.dist]
+    st = make(int(n_full * a.scale))
     s = st.symbols()
-    enc = R.encode_with_splits(s, st.n_bits, max(1, min(65536, len(s) // 4096)))
-    return ZIPF_WORKLOAD, [st], [s], [enc], [R.combine_splits(enc, a.splits)]
+    enc_splits = 64 if a.dist == "laplace" else max(1, min(65536, len(s) // 4096))
+    enc = R.encode_with_splits(s, st.n_bits, enc_splits)
+    desc = (f"single stream: {what}, W=32, encoded at {enc_splits} splits and combined to the decoder's "
+            f"split count")
+    return desc, [st], [s], [enc], [R.combine_splits(enc, a.splits)]
 
 
 def run_ours(a):
@@ -433,7 +444,7 @@ def run_ours(a):
     peaks = measured_peaks()
     achieved = (out_bytes + in_bytes) / (mean_ms * 1e-3) / 1e9
     tkey = (f"batch w{opts['warps_per_cta']} s{split_symbols}" if batch
-            else f"zipf w{opts['warps_per_cta']} k{a.splits}")
+            else f"{a.dist} w{opts['warps_per_cta']} k{a.splits}")
     traffic = recorded_traffic(tkey) if a.scale == 1.0 and a.streams == workloads.BATCH_STREAMS else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
@@ -489,6 +500,12 @@ def run_serve(a):
 
 if __name__ == "__main__":
     args = _args()
+    if args.workload == "zipf":
+        args.workload, args.dist = "single", "zipf"
+    if args.workload == "single" and args.dist == "laplace" and args.splits == 9472:
+        args.splits = 64
+    if args.workload == "single" and args.dist == "laplace":
+        args.sweep = [k for k in args.sweep if k <= 64] or [64, 16, 1]
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":
