@@ -55,7 +55,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="batch", choices=["batch", "single", "zipf", "serve"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "single", "zipf", "serve", "conventional"])
     ap.add_argument("--dist", default="zipf", choices=["zipf", "skewed", "uniform", "gauss16", "laplace"],
                     help="single: which stream (zipf 1 GiB, the 256 MiB extremes, laplace 1 MiB)")
     ap.add_argument("--splits", type=int, default=9472, help="zipf: decoder split count")
@@ -298,6 +298,71 @@ def make_workload(a, R, rank):
     return desc, [st], [s], [enc], [R.combine_splits(enc, a.splits)]
 
 
+def run_conventional(a):
+    """--workload conventional: Recoil splits vs the conventional scheme (Sec. 2.3) on the same input.
+
+    The 1 GiB Zipf input is decoded (1) as one Recoil stream combined to P splits and (2) cut into P
+    equal partitions, each an independent interleaved stream with its own final states under the same
+    quantised model (the paper's baseline B). Same kernel, same launch shape; reports both decode
+    rates and both compressed sizes (Recoil: bitstream + unpacked split metadata)."""
+    import torch
+    import paper_2306_12141_b300 as R
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    st = workloads.zipf_1gib(int((1 << 30) * a.scale))
+    s = st.symbols()
+    enc = R.encode_with_splits(s, st.n_bits, max(1, min(65536, len(s) // 4096)))
+    P = a.splits
+    rec = R.combine_splits(enc, P)
+    freq = R.stream_freq(enc)
+    parts = np.array_split(s, P)
+    with ThreadPoolExecutor(max(1, min(64, os.cpu_count() or 1))) as ex:
+        conv = list(ex.map(lambda p: R.encode_with_table(p, st.n_bits, freq, 1), parts))
+    warps = a.warps or 16
+    cs = torch.cuda.Stream(device=dev)
+    ref = torch.from_numpy(s).to(dev)
+    res = {}
+    for name, streams in (("recoil", [rec]), ("conventional", conv)):
+        plan = R.Plan(streams, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+        ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
+        out = torch.empty(len(s), dtype=torch.uint8, device=dev)
+        if name == "recoil":
+            ptrs = [out.data_ptr()]
+        else:
+            offs = np.concatenate([[0], np.cumsum([len(p) for p in parts])])
+            ptrs = [out.data_ptr() + int(o) for o in offs[:-1]]
+        with torch.cuda.stream(cs):
+            plan.upload(ws, stream=cs)
+            for _ in range(a.warmup):
+                plan.decode(ptrs, cs)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+            for e0, e1 in ev:
+                e0.record(cs)
+                plan.decode(ptrs, cs)
+                e1.record(cs)
+            torch.cuda.synchronize()
+            assert plan.errors(cs) == 0
+        assert torch.equal(out, ref), name
+        ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+        infos = [x.info for x in streams]
+        nbytes = sum(i["bitstream_bytes"] + i["metadata_bytes"] for i in infos)
+        if name == "conventional":
+            nbytes += 8 * len(streams)                     # offset table of the partitions
+        res[name] = {"gbs": len(s) / (ms * 1e-3) / 1e9, "ms": ms, "compressed_bytes": int(nbytes),
+                     "streams": len(streams), "splits": sum(i["n_entries"] for i in infos)}
+        del ws, out
+    line = {"metric": METRIC, "value": res["recoil"]["gbs"], "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": res["recoil"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"Recoil vs conventional partitioning at {P} splits/partitions on 1 GiB of "
+                                   f"Zipf(1.2) bytes, n=12, same quantised model, {warps} warps per CTA",
+                       "scale": a.scale},
+            "recoil": res["recoil"], "conventional": res["conventional"],
+            "recoil_vs_conventional_speed": res["recoil"]["gbs"] / res["conventional"]["gbs"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(a):
     import torch
     import paper_2306_12141_b300 as R
@@ -508,6 +573,8 @@ if __name__ == "__main__":
         args.sweep = [k for k in args.sweep if k <= 64] or [64, 16, 1]
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "conventional":
+        run_conventional(args)
     elif args.workload == "serve":
         if args.serve_requests == 5000:
             args.serve_requests = 20000

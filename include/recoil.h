@@ -87,6 +87,17 @@ int recoil_encode_with_splits(const void* syms, uint64_t n_syms, const recoil_pa
                               uint32_t max_splits, recoil_stream** out);
 
 /*
+ * As recoil_encode_with_splits, with the quantised PDF given instead of
+ * counted: freq[alphabet] sums to 2^n and is positive for every symbol that
+ * occurs (e.g. one static model shared by many streams, or by the partitions
+ * of the conventional scheme the paper compares with, Sec. 2.3).
+ * Errors: as above, and EINVAL for a table that is missing, does not sum to
+ * 2^n, or gives an occurring symbol no probability.
+ */
+int recoil_encode_with_table(const void* syms, uint64_t n_syms, const recoil_params* params, const uint32_t* freq,
+                             uint32_t alphabet, uint32_t max_splits, recoil_stream** out);
+
+/*
  * Combine splits (Sec. 3.3, 4.2): a new stream with min(target_splits, K)
  * entries, keeping entries ceil((k+1) K / M') - 1 of the K entries of `in`
  * (the final-state entry always stays). The bitstream is shared, not copied;

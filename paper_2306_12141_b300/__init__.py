@@ -77,7 +77,7 @@ EXPORTS = [
     "recoil_decode", "recoil_decode_batch", "recoil_decode_noalloc", "recoil_autotune",
     "recoil_autotune_workspace_size", "recoil_serve", "recoil_serve_arena_size",
     "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
-    "recoil_pipeline_free", "recoil_shard",
+    "recoil_pipeline_free", "recoil_shard", "recoil_encode_with_table",
 ]
 
 _lib = None
@@ -94,6 +94,7 @@ def lib():
         pp = C.POINTER(C.c_void_p)
         L.recoil_encode_with_splits.argtypes = [vp, u64, C.POINTER(Params), u32, pp]
         L.recoil_combine_splits.argtypes = [vp, u32, pp]
+        L.recoil_encode_with_table.argtypes = [vp, u64, C.POINTER(Params), vp, u32, u32, pp]
         L.recoil_stream_info.argtypes = [vp, C.POINTER(Info)]
         L.recoil_stream_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.recoil_stream_import.argtypes = [C.POINTER(Params), u64, u32, vp, vp, u64, vp, u32, vp, vp, vp, pp]
@@ -195,6 +196,18 @@ def recoil_encode_with_splits(symbols: np.ndarray, n_bits: int, max_splits: int)
     return Stream(h.value)
 
 
+def recoil_encode_with_table(symbols: np.ndarray, n_bits: int, freq, max_splits: int) -> Stream:
+    s = np.ascontiguousarray(symbols)
+    if s.dtype not in (np.uint8, np.uint16):
+        raise TypeError("symbols must be uint8 or uint16")
+    f = np.ascontiguousarray(freq, dtype=np.uint32)
+    p = Params(n_bits, s.dtype.itemsize)
+    h = C.c_void_p()
+    _check(lib().recoil_encode_with_table(s.ctypes.data if s.size else None, s.size, C.byref(p), _ptr(f), len(f),
+                                          max_splits, C.byref(h)))
+    return Stream(h.value)
+
+
 def recoil_combine_splits(stream: Stream, target_splits: int) -> Stream:
     h = C.c_void_p()
     _check(lib().recoil_combine_splits(stream.handle, target_splits, C.byref(h)))
@@ -222,6 +235,13 @@ def recoil_stream_export(stream: Stream) -> dict:
                                                        ("freq", "words", "final", "entry_word",
                                                         "entry_index", "entry_state")]))
     return out
+
+
+def stream_freq(stream: Stream) -> np.ndarray:
+    """The stream's quantised PDF only (recoil_stream_export with every other part skipped)."""
+    f = np.zeros(stream_info(stream)["alphabet"], dtype=np.uint32)
+    _check(lib().recoil_stream_export(stream.handle, _ptr(f), None, None, None, None, None))
+    return f
 
 
 def recoil_stream_import(n_bits: int, sym_bytes: int, n_syms: int, freq, words, final,
@@ -486,6 +506,7 @@ def recoil_decode_noalloc(stream: Stream, d_words, words_bytes: int, d_out, cuda
 # short aliases
 encode_with_splits = recoil_encode_with_splits
 combine_splits = recoil_combine_splits
+encode_with_table = recoil_encode_with_table
 stream_info = recoil_stream_info
 stream_export = recoil_stream_export
 stream_import = recoil_stream_import

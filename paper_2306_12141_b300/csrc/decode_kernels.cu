@@ -306,16 +306,19 @@ __global__ void __launch_bounds__(WARPS * 32, Residency<WARPS>::kMinBlocks) deco
       __syncthreads();
     }
     if ((uint32_t)warp < item.count) {
+      // the entry's own stream: an item may span streams that share one table
+      const DevEntry* ent = a.entries + item.entry + warp;
+      const uint32_t sid = ent->stream;
       EntryDecoder<KIND> d;
       d.T.bind(smem, st);
-      d.words = a.word_pool + st.words;
+      d.words = a.word_pool + a.streams[sid].words;
       d.ring = ring;
-      d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[item.stream]);
+      d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[sid]);
       d.n = st.n_bits;
       d.mask = (1u << st.n_bits) - 1u;
       d.gt = lanemask_gt();
       d.lane = threadIdx.x & 31;
-      d.run(a.entries + item.entry + warp, a.control, item.entry + warp);
+      d.run(ent, a.control, item.entry + warp);
     }
     if (!a.persistent) break;
     __syncthreads();

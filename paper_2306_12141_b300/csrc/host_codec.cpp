@@ -240,22 +240,17 @@ extern "C" {
 
 const char* recoil_last_error(void) { return g_last_error.c_str(); }
 
-int recoil_encode_with_splits(const void* syms, uint64_t n_syms, const recoil_params* params,
-                              uint32_t max_splits, recoil_stream** out) {
-  clear_error();
-  if (!params || !out || (!syms && n_syms)) return fail(RECOIL_EINVAL, "null argument");
-  if (params->n_bits < 1 || params->n_bits > 16) return fail(RECOIL_EINVAL, "n_bits must be in [1, 16]");
-  if (params->sym_bytes != 1 && params->sym_bytes != 2) return fail(RECOIL_EINVAL, "sym_bytes must be 1 or 2");
-  if (n_syms >= (1ull << 31)) return fail(RECOIL_EINVAL, "streams are limited to 2^31 - 1 symbols");
-  if (max_splits < 1) max_splits = 1;
-  *out = nullptr;
+}  // extern "C"
+
+// Encode with a given quantised PDF (validated by the callers), place splits.
+static int encode_common(const void* syms, uint64_t n_syms, const recoil_params* params, std::vector<uint32_t> freq,
+                         uint32_t max_splits, recoil_stream** out) {
   try {
     std::unique_ptr<recoil_stream> s(new recoil_stream());
     s->n_bits = params->n_bits;
     s->sym_bytes = params->sym_bytes;
     s->n_syms = n_syms;
-    int rc = make_table_syms(syms, n_syms, params->sym_bytes, params->n_bits, s->freq);
-    if (rc) return rc;
+    s->freq = std::move(freq);
     const uint32_t n = params->n_bits;
     std::vector<EncSym> tab(s->freq.size());
     uint32_t F = 0;
@@ -289,6 +284,50 @@ int recoil_encode_with_splits(const void* syms, uint64_t n_syms, const recoil_pa
   } catch (const std::bad_alloc&) {
     return fail(RECOIL_ENOMEM, "host allocation failed");
   }
+}
+
+static int check_params(const void* syms, uint64_t n_syms, const recoil_params* params, recoil_stream** out) {
+  if (!params || !out || (!syms && n_syms)) return fail(RECOIL_EINVAL, "null argument");
+  if (params->n_bits < 1 || params->n_bits > 16) return fail(RECOIL_EINVAL, "n_bits must be in [1, 16]");
+  if (params->sym_bytes != 1 && params->sym_bytes != 2) return fail(RECOIL_EINVAL, "sym_bytes must be 1 or 2");
+  if (n_syms >= (1ull << 31)) return fail(RECOIL_EINVAL, "streams are limited to 2^31 - 1 symbols");
+  *out = nullptr;
+  return RECOIL_OK;
+}
+
+extern "C" {
+
+int recoil_encode_with_splits(const void* syms, uint64_t n_syms, const recoil_params* params,
+                              uint32_t max_splits, recoil_stream** out) {
+  clear_error();
+  int rc = check_params(syms, n_syms, params, out);
+  if (rc) return rc;
+  std::vector<uint32_t> freq;
+  try {
+    rc = make_table_syms(syms, n_syms, params->sym_bytes, params->n_bits, freq);
+  } catch (const std::bad_alloc&) {
+    return fail(RECOIL_ENOMEM, "host allocation failed");
+  }
+  if (rc) return rc;
+  return encode_common(syms, n_syms, params, std::move(freq), std::max<uint32_t>(max_splits, 1), out);
+}
+
+int recoil_encode_with_table(const void* syms, uint64_t n_syms, const recoil_params* params, const uint32_t* freq,
+                             uint32_t alphabet, uint32_t max_splits, recoil_stream** out) {
+  clear_error();
+  int rc = check_params(syms, n_syms, params, out);
+  if (rc) return rc;
+  if (!freq || alphabet < 1 || alphabet > (params->sym_bytes == 1 ? 256u : 65536u))
+    return fail(RECOIL_EINVAL, "frequency table missing or alphabet out of range");
+  uint64_t sum = 0;
+  for (uint32_t k = 0; k < alphabet; k++) sum += freq[k];
+  if (sum != (1ull << params->n_bits)) return fail(RECOIL_EINVAL, "frequencies must sum to 2^n");
+  for (uint64_t i = 0; i < n_syms; i++) {
+    const uint32_t v = params->sym_bytes == 1 ? ((const uint8_t*)syms)[i] : ((const uint16_t*)syms)[i];
+    if (v >= alphabet || !freq[v]) return fail(RECOIL_EINVAL, "a symbol has no probability in the table");
+  }
+  return encode_common(syms, n_syms, params, std::vector<uint32_t>(freq, freq + alphabet),
+                       std::max<uint32_t>(max_splits, 1), out);
 }
 
 int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_stream** out) {

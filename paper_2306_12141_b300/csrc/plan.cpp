@@ -65,11 +65,13 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
 }  // namespace
 
 // Device entries of a stream: kept regular entries in order, then the final one.
-void build_entries(const Stream& s, std::vector<DevEntry>& out) {
+void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>& out) {
   const uint32_t N = (uint32_t)s.n_syms;
   uint32_t prev_m = 0;
   for (const Entry& e : s.entries) {
     DevEntry d;
+    std::memset(&d, 0, sizeof d);
+    d.stream = stream_index;
     uint32_t mn = e.idx[0], mx = e.idx[0];
     for (int j = 0; j < kW; j++) {
       d.x0[j] = e.y[j];
@@ -85,6 +87,8 @@ void build_entries(const Stream& s, std::vector<DevEntry>& out) {
     out.push_back(d);
   }
   DevEntry d;
+  std::memset(&d, 0, sizeof d);
+  d.stream = stream_index;
   int32_t top = 0;
   for (int j = 0; j < kW; j++) {
     d.x0[j] = s.final_x[j];
@@ -136,8 +140,15 @@ struct recoil_plan {
   }
 };
 
+// Symbols one entry's walk visits (for longest-first ordering of work items).
+static uint32_t entry_work(const DevEntry& de) {
+  const int64_t span = (int64_t)de.g_top * kW - (int64_t)de.lo;
+  return (uint32_t)std::max<int64_t>(0, std::min<int64_t>(span, 0x7fffffff));
+}
+
 static int plan_build(recoil_plan* P) {
   const uint32_t count = (uint32_t)P->streams.size();
+  const bool per_stream = P->opts.flags & RECOIL_BATCH_PER_STREAM;
   const uint32_t warps = P->warps;
   std::vector<DevStream> ds(count);
   std::vector<DevEntry> entries;
@@ -171,19 +182,27 @@ static int plan_build(recoil_plan* P) {
     P->kind_smem[kind] = std::max<uint32_t>(P->kind_smem[kind], d.table_bytes);
 
     const size_t first = entries.size();
-    build_entries(s, entries);
-    for (size_t e = first; e < entries.size(); e += warps) {
+    build_entries(s, i, entries);
+    // a stream whose tables equal the previous stream's may fill up the
+    // previous stream's last work item (one staged table serves both)
+    const bool same_table = i > 0 && !per_stream && !items.empty() && items.back().kind == kind &&
+                            P->streams[i - 1]->n_bits == s.n_bits && P->streams[i - 1]->sym_bytes == s.sym_bytes &&
+                            P->streams[i - 1]->freq == s.freq &&
+                            items.back().it.entry + items.back().it.count == first;
+    size_t e = first;
+    if (same_table && items.back().it.count < warps) {
+      const uint32_t take = (uint32_t)std::min<size_t>(warps - items.back().it.count, entries.size() - e);
+      items.back().it.count += take;
+      for (uint32_t k = 0; k < take; k++) items.back().it.work = std::max(items.back().it.work, entry_work(entries[e + k]));
+      e += take;
+    }
+    for (; e < entries.size(); e += warps) {
       ItemK ik;
       ik.it.stream = i;
       ik.it.entry = (uint32_t)e;
       ik.it.count = (uint32_t)std::min<size_t>(warps, entries.size() - e);
-      uint32_t work = 0;
-      for (uint32_t k = 0; k < ik.it.count; k++) {
-        const DevEntry& de = entries[e + k];
-        const int64_t span = (int64_t)de.g_top * kW - (int64_t)de.lo;
-        work = std::max<uint32_t>(work, (uint32_t)std::max<int64_t>(0, std::min<int64_t>(span, 0x7fffffff)));
-      }
-      ik.it.work = work;
+      ik.it.work = 0;
+      for (uint32_t k = 0; k < ik.it.count; k++) ik.it.work = std::max(ik.it.work, entry_work(entries[e + k]));
       ik.kind = kind;
       items.push_back(ik);
     }
@@ -193,7 +212,6 @@ static int plan_build(recoil_plan* P) {
       return fail(RECOIL_EINVAL, "decoder tables too large for shared memory (alphabet or n too large)");
   }
   // item order: by kind; persistent mode longest first, per-stream mode by stream
-  const bool per_stream = P->opts.flags & RECOIL_BATCH_PER_STREAM;
   const bool sort = !per_stream && !(P->opts.flags & RECOIL_BATCH_NO_SORT);
   std::stable_sort(items.begin(), items.end(), [&](const ItemK& a, const ItemK& b) {
     if (per_stream) return a.it.stream < b.it.stream;

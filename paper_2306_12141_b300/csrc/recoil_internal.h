@@ -71,8 +71,10 @@ struct alignas(16) DevEntry {
   uint32_t hi1;              // one past the last owned symbol (lo == hi1: nothing owned)
   uint32_t x0[kW];           // state a coder takes when it joins
   int32_t act[kW];           // group at which a coder joins (takes x0, renormalises)
+  uint32_t stream;           // stream (index into the launch's streams) the entry belongs to
+  uint32_t pad[3];
 };
-static_assert(sizeof(DevEntry) == 16 + 8 * kW, "DevEntry layout");
+static_assert(sizeof(DevEntry) == 32 + 8 * kW, "DevEntry layout");
 
 struct alignas(16) DevStream {
   uint64_t words;            // element offset of the stream's words in the word pool (multiple of 256)
@@ -88,7 +90,8 @@ struct alignas(16) DevStream {
 };
 static_assert(sizeof(DevStream) == 48, "DevStream layout");
 
-// A unit of work for one CTA: up to warps_per_cta consecutive entries of one stream.
+// A unit of work for one CTA: up to warps_per_cta consecutive entries, of one
+// stream or of consecutive streams whose decoder tables are identical.
 struct alignas(16) DevItem {
   uint32_t stream;
   uint32_t entry;            // first DevEntry
@@ -149,7 +152,7 @@ struct recoil_plan;
 namespace recoil {
 void plan_image(const recoil_plan* plan, PlanImage* out);
 // Device entries of a stream's kept splits, the final-state entry last (plan.cpp).
-void build_entries(const Stream& s, std::vector<DevEntry>& out);
+void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>& out);
 // Upload the bulk region (words, tables) and/or the descriptors of a plan.
 int plan_upload_parts(recoil_plan* plan, void* d_ws, size_t ws_bytes, cudaStream_t s, bool bulk, bool meta);
 // Bytes of the bulk region at the start of a plan's workspace.

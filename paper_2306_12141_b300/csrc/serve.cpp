@@ -308,7 +308,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
           }
           std::unique_ptr<recoil_stream> cg(c);
           const size_t first = ents.size();
-          build_entries(*c, ents);
+          build_entries(*c, (uint32_t)k, ents);
           results[r].splits = (uint32_t)(ents.size() - first);
           results[r].launch = launches;
           ds[k] = pool_ds[req_stream[r]];

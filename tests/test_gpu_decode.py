@@ -307,3 +307,18 @@ def test_distribution_extremes_full_size(recoil_lib, make):
         plan.decode([out.data_ptr()], cs)
         assert plan.errors(cs) == 0
         assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("warps", [1, 4, 16])
+def test_partitions_sharing_one_model(recoil_lib, warps):
+    """Conventional partitioning (Sec. 2.3): independent streams with one shared table.
+
+    Work items then span several streams, one staged table serving all of them."""
+    R = recoil_lib
+    s = workloads.Stream("z", 3_000_000, 1, 12, "zipf", {"s": 1.2}, seed=72).symbols()
+    f = oracle.quantize(np.bincount(s, minlength=256), 12)
+    cuts = np.sort(np.random.default_rng(3).choice(len(s), size=150, replace=False))
+    parts = np.split(s, cuts)
+    streams = [R.encode_with_table(p, 12, f, 1 + len(p) // 40_000) for p in parts]
+    outs = gpu_decode(R, streams, {"warps_per_cta": warps})
+    assert np.array_equal(np.concatenate(outs), s)

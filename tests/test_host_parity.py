@@ -105,3 +105,23 @@ def test_import_round_trip_and_validation(recoil_lib):
     fin[5] = 10
     assert bad(final=fin) == R.ECORRUPT                            # final state below L
     assert bad(n_bits=17) == R.EINVAL
+
+
+def test_encode_with_given_table_matches_oracle(recoil_lib):
+    R = recoil_lib
+    s = workloads.Stream("z", 200_000, 1, 12, "zipf", {"s": 1.2}, seed=71).symbols()
+    f = oracle.quantize(np.bincount(s, minlength=256), 12)
+    parts = [s[i:i + 20_000] for i in range(0, len(s), 20_000)]      # partitions share one model
+    for part in parts:
+        p = R.encode_with_table(part, 12, f, 4)
+        words, final, ev_sym, ev_y = oracle.encode(part, f, 12)
+        e = p.export()
+        assert np.array_equal(e["freq"], f) and np.array_equal(e["words"], words)
+        assert np.array_equal(e["final"], final)
+    bad = f.copy()
+    bad[s[0]] = 0
+    bad[255] += f[s[0]]
+    with pytest.raises(R.RecoilError):
+        R.encode_with_table(s, 12, bad, 4)                        # an occurring symbol without probability
+    with pytest.raises(R.RecoilError):
+        R.encode_with_table(s, 12, f[:-1], 4) if f[-1] else R.encode_with_table(s, 12, f * 2, 4)
