@@ -135,6 +135,40 @@ int recoil_stream_import(const recoil_params* params, uint64_t n_syms, uint32_t 
  * copies). Needs a CUDA driver. Errors: ECUDA. */
 int recoil_stream_pin(recoil_stream* s);
 
+/*
+ * Serialised form of a stream: what a content server stores and sends
+ * (Sec. 3.3). Little-endian container: "RCL1", n_bits (u8), sym_bytes (u8),
+ * two zero bytes, alphabet (u32), the quantised PDF (u32 each), the W final
+ * states (u32 each), the word count (u64), the words (u16 each), the length of
+ * the metadata section in bytes (u64), then the split metadata packed as in
+ * Sec. 4.3:
+ *   - header: M = splits counting the final-state one (32 bits), words B (64),
+ *     symbols N (64);
+ *   - the split words q_i, i = 1..M-1, as differences from i*ceil(B/M), and
+ *     the anchors (largest group ID of a split point, group ID = recorded
+ *     index / W + 1, Table 2) as differences from i*ceil(ceil(N/W)/M): two
+ *     signed series (Table 1);
+ *   - per split point its W states as-is (16 bits each, Lemma 3.1) and the
+ *     series of anchor minus each coder's group ID (unsigned, Table 2).
+ * A series is (w-1) in a 4-bit (unsigned) or 5-bit (signed) field, then each
+ * value in w bits, a signed value after a sign bit; w = the bit length of the
+ * largest magnitude, 1 when all are zero. Bits go most significant first; the
+ * section is padded with zero bits to a whole byte. Combine first
+ * (recoil_combine_splits) to send fewer splits.
+ *
+ * recoil_serialized_size: *bytes = the container's size, *metadata_bytes (may
+ *   be NULL) = the packed metadata section's size. Errors: EINVAL (null, or a
+ *   group difference wider than 16 bits / an offset wider than 32 bits).
+ * recoil_serialize: writes the container into buf (cap bytes; ENOMEM if too
+ *   small) and its size into *written. Errors: EINVAL, ENOMEM.
+ * recoil_deserialize: parses size bytes at buf into a new stream (freed with
+ *   recoil_free), validated as recoil_stream_import does. Errors: EINVAL
+ *   (null), ECORRUPT (bad magic, truncated or inconsistent data), ENOMEM.
+ */
+int recoil_serialized_size(const recoil_stream* s, uint64_t* bytes, uint64_t* metadata_bytes);
+int recoil_serialize(const recoil_stream* s, void* buf, uint64_t cap, uint64_t* written);
+int recoil_deserialize(const void* buf, uint64_t size, recoil_stream** out);
+
 void recoil_free(recoil_stream* s);
 const char* recoil_last_error(void);
 

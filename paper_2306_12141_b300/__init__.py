@@ -78,6 +78,7 @@ EXPORTS = [
     "recoil_autotune_workspace_size", "recoil_serve", "recoil_serve_arena_size",
     "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
     "recoil_pipeline_free", "recoil_shard", "recoil_encode_with_table",
+    "recoil_serialized_size", "recoil_serialize", "recoil_deserialize",
 ]
 
 _lib = None
@@ -99,6 +100,9 @@ def lib():
         L.recoil_stream_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.recoil_stream_import.argtypes = [C.POINTER(Params), u64, u32, vp, vp, u64, vp, u32, vp, vp, vp, pp]
         L.recoil_stream_pin.argtypes = [vp]
+        L.recoil_serialized_size.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
+        L.recoil_serialize.argtypes = [vp, vp, u64, C.POINTER(u64)]
+        L.recoil_deserialize.argtypes = [vp, u64, pp]
         L.recoil_free.argtypes = [vp]
         L.recoil_free.restype = None
         L.recoil_last_error.restype = C.c_char_p
@@ -262,6 +266,30 @@ def recoil_stream_import(n_bits: int, sym_bytes: int, n_syms: int, freq, words, 
 
 def recoil_stream_pin(stream: Stream) -> None:
     _check(lib().recoil_stream_pin(stream.handle))
+
+
+def recoil_serialized_size(stream: Stream) -> tuple[int, int]:
+    """(container bytes, packed split-metadata bytes) of the stream's serialised form (Sec. 4.3)."""
+    total, meta = C.c_uint64(), C.c_uint64()
+    _check(lib().recoil_serialized_size(stream.handle, C.byref(total), C.byref(meta)))
+    return total.value, meta.value
+
+
+def recoil_serialize(stream: Stream) -> bytes:
+    """The stream's serialised form: model, final states, words and packed split metadata."""
+    total, _ = recoil_serialized_size(stream)
+    buf = C.create_string_buffer(max(1, total))
+    written = C.c_uint64()
+    _check(lib().recoil_serialize(stream.handle, buf, total, C.byref(written)))
+    return buf.raw[:written.value]
+
+
+def recoil_deserialize(data: bytes) -> Stream:
+    """Parse a serialised stream (validated like recoil_stream_import)."""
+    data = bytes(data)
+    h = C.c_void_p()
+    _check(lib().recoil_deserialize(data, len(data), C.byref(h)))
+    return Stream(h.value)
 
 
 # -------------------------------------------------------------------- plans
@@ -511,6 +539,9 @@ stream_info = recoil_stream_info
 stream_export = recoil_stream_export
 stream_import = recoil_stream_import
 stream_pin = recoil_stream_pin
+serialized_size = recoil_serialized_size
+serialize = recoil_serialize
+deserialize = recoil_deserialize
 workspace_size = recoil_workspace_size
 decode = recoil_decode
 decode_batch = recoil_decode_batch
