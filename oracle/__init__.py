@@ -3,7 +3,8 @@
 Python face of ``recoil_oracle.c``: a plain, slow, single-threaded CPU
 restatement of the Recoil method (rANS Eqs. 1-4, interleaving Sec. 2.2,
 Lemma 3.1, split metadata and the three decoding phases of Sec. 4.1, the
-heuristic of Def. 4.1 / Eq. 7, combining of Sec. 3.3). Only ``tests/``,
+heuristic of Def. 4.1 / Eq. 7, combining of Sec. 3.3, adaptive coding keyed
+by the symbol index of Sec. 3.1). Only ``tests/``,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may use
 it. It shares no code with the CUDA library and imports nothing from it.
 
@@ -67,6 +68,14 @@ def lib():
                                            i32, p, p, i64, i64, i64, p, p, p]
         L.oracle_decode_splits.argtypes = [p, i64, p, i64, p, i32, i32, i32, i32, i32,
                                            i64, p, p, p, p]
+        L.oracle_encode_adaptive.argtypes = [p, i64, p, i32, i32, p, i32, i32, i32, i32, p, i64, p, p, p]
+        L.oracle_encode_adaptive.restype = i64
+        L.oracle_decode_serial_adaptive.argtypes = [p, i64, p, i64, p, i32, i32, p, i32, i32, i32, i32,
+                                                    p, p, p]
+        L.oracle_decode_splits_adaptive.argtypes = [p, i64, p, i64, p, i32, i32, p, i32, i32, i32, i32,
+                                                    i64, p, p, p, p]
+        L.oracle_decode_thread_adaptive.argtypes = [p, i64, p, i64, p, i32, i32, p, i32, i32, i32, i32,
+                                                    i32, p, p, i64, i64, i64, p]
         _lib = L
     return _lib
 
@@ -130,6 +139,45 @@ def decode_serial(B, xf, N: int, f, n: int, W: int = W_DEFAULT, lgL: int = LGL_D
     return out, end_x, int(end_p[0])
 
 
+def encode_adaptive(sym, tid, tables, n: int, W: int = W_DEFAULT, lgL: int = LGL_DEFAULT,
+                    b: int = B_DEFAULT):
+    """Encode with PDF row tid[i] of tables (T x A) for symbol i (Sec. 3.1). Same returns as encode."""
+    s = _u32(sym)
+    t = _u32(tid)
+    tab = np.ascontiguousarray(np.atleast_2d(tables), dtype=np.uint32)
+    N = len(s)
+    if len(t) != N:
+        raise ValueError("one table index per symbol")
+    cap = N + W + 16
+    B = np.zeros(cap, dtype=np.uint16)
+    xf = np.zeros(W, dtype=np.uint32)
+    ev_sym = np.zeros(cap, dtype=np.int64)
+    ev_y = np.zeros(cap, dtype=np.uint32)
+    nw = lib().oracle_encode_adaptive(_ptr(s), N, _ptr(tab), tab.shape[0], tab.shape[1], _ptr(t), W, n, lgL, b,
+                                      _ptr(B), cap, _ptr(xf), _ptr(ev_sym), _ptr(ev_y))
+    if nw < 0:
+        raise ValueError(f"oracle_encode_adaptive failed ({nw})")
+    return B[:nw].copy(), xf, ev_sym[:nw].copy(), ev_y[:nw].copy()
+
+
+def decode_serial_adaptive(B, xf, tid, tables, n: int, W: int = W_DEFAULT, lgL: int = LGL_DEFAULT,
+                           b: int = B_DEFAULT):
+    """Serial decode with the adaptive model. Returns (out, end_x, end_p)."""
+    B = np.ascontiguousarray(B, dtype=np.uint16)
+    t = _u32(tid)
+    tab = np.ascontiguousarray(np.atleast_2d(tables), dtype=np.uint32)
+    N = len(t)
+    out = np.zeros(N, dtype=np.uint32)
+    end_x = np.zeros(W, dtype=np.uint32)
+    end_p = np.zeros(1, dtype=np.int64)
+    rc = lib().oracle_decode_serial_adaptive(_ptr(B), len(B), _ptr(_u32(xf)), N, _ptr(tab), tab.shape[0],
+                                             tab.shape[1], _ptr(t), W, n, lgL, b, _ptr(out), _ptr(end_x),
+                                             _ptr(end_p))
+    if rc:
+        raise ValueError(f"oracle_decode_serial_adaptive failed ({rc})")
+    return out, end_x, int(end_p[0])
+
+
 def scan(ev_sym, ev_y, q: int, W: int = W_DEFAULT):
     """Backward scan from word q (Sec. 4.1). Returns (usable, idx[W], y[W], word[W])."""
     idx = np.zeros(W, dtype=np.int64)
@@ -165,7 +213,7 @@ class OracleStream:
     W: int
     lgL: int
     b: int
-    f: np.ndarray          # quantised PDF
+    f: np.ndarray          # quantised PDF (adaptive: T x A, one row per table)
     words: np.ndarray      # u16 bitstream
     final: np.ndarray      # u32[W] final states
     ev_sym: np.ndarray     # per word: symbol index whose coding triggered it
@@ -173,6 +221,7 @@ class OracleStream:
     q: np.ndarray          # split words of the regular entries (increasing)
     idx: np.ndarray        # K x W recorded symbol indices (last row: final entry, unused)
     y: np.ndarray          # K x W states (last row: final states)
+    tid: np.ndarray | None = None   # adaptive model: PDF row of every symbol index (Sec. 3.1)
 
     @property
     def K(self) -> int:
@@ -205,13 +254,25 @@ def encode_with_splits(sym, n: int, M: int, W: int = W_DEFAULT, lgL: int = LGL_D
     return OracleStream(len(s), n, W, lgL, b, f, words, final, ev_sym, ev_y, qs, idx, y)
 
 
+def encode_adaptive_with_splits(sym, tid, tables, n: int, M: int, W: int = W_DEFAULT,
+                                lgL: int = LGL_DEFAULT, b: int = B_DEFAULT) -> OracleStream:
+    """Adaptive encode (PDF row tid[i] for symbol i) and M splits placed by the heuristic."""
+    s = _u32(sym)
+    tab = np.ascontiguousarray(np.atleast_2d(tables), dtype=np.uint32)
+    words, final, ev_sym, ev_y = encode_adaptive(s, tid, tab, n, W, lgL, b)
+    qs = heuristic(ev_sym, ev_y, len(s), M, W)
+    idx, y = entries_for(ev_sym, ev_y, qs, W)
+    y[-1] = final
+    return OracleStream(len(s), n, W, lgL, b, tab, words, final, ev_sym, ev_y, qs, idx, y, _u32(tid))
+
+
 def combined(st: OracleStream, Mp: int) -> OracleStream:
     """The same stream with only Mp entries kept (the final entry always stays)."""
     keep = combine_keep(st.K, Mp)
     regular = [k for k in keep if k < st.K - 1]
     return OracleStream(st.N, st.n, st.W, st.lgL, st.b, st.f, st.words, st.final, st.ev_sym,
                         st.ev_y, st.q[regular], np.vstack([st.idx[regular], st.idx[-1:]]),
-                        np.vstack([st.y[regular], st.y[-1:]]))
+                        np.vstack([st.y[regular], st.y[-1:]]), st.tid)
 
 
 def decode_splits(st: OracleStream) -> np.ndarray:
@@ -220,9 +281,16 @@ def decode_splits(st: OracleStream) -> np.ndarray:
     idx = _i64(st.idx)
     y = _u32(st.y)
     q = _i64(np.concatenate([st.q, [0]]))
-    rc = lib().oracle_decode_splits(_ptr(st.words), len(st.words), _ptr(st.final), st.N,
-                                    _ptr(_u32(st.f)), len(st.f), st.W, st.n, st.lgL, st.b,
-                                    st.K, _ptr(idx), _ptr(y), _ptr(q), _ptr(out))
+    if st.tid is not None:
+        tab = np.ascontiguousarray(st.f, dtype=np.uint32)
+        rc = lib().oracle_decode_splits_adaptive(_ptr(st.words), len(st.words), _ptr(st.final), st.N,
+                                                 _ptr(tab), tab.shape[0], tab.shape[1], _ptr(_u32(st.tid)),
+                                                 st.W, st.n, st.lgL, st.b, st.K, _ptr(idx), _ptr(y), _ptr(q),
+                                                 _ptr(out))
+    else:
+        rc = lib().oracle_decode_splits(_ptr(st.words), len(st.words), _ptr(st.final), st.N,
+                                        _ptr(_u32(st.f)), len(st.f), st.W, st.n, st.lgL, st.b,
+                                        st.K, _ptr(idx), _ptr(y), _ptr(q), _ptr(out))
     if rc:
         raise ValueError(f"oracle_decode_splits failed ({rc})")
     return out
@@ -247,6 +315,17 @@ def decode_thread(st: OracleStream, k: int, trace: bool = False, out: np.ndarray
     idx = _i64(st.idx[k])
     y = _u32(st.y[k])
     q = 0 if is_final else int(st.q[k])
+    if st.tid is not None:
+        if trace:
+            raise ValueError("traces are kept for the static model only")
+        tab = np.ascontiguousarray(st.f, dtype=np.uint32)
+        rc = lib().oracle_decode_thread_adaptive(_ptr(st.words), len(st.words), _ptr(st.final), st.N,
+                                                 _ptr(tab), tab.shape[0], tab.shape[1], _ptr(_u32(st.tid)),
+                                                 st.W, st.n, st.lgL, st.b, is_final, _ptr(idx), _ptr(y), q,
+                                                 lo, hi, _ptr(out))
+        if rc:
+            raise ValueError(f"oracle_decode_thread_adaptive failed ({rc})")
+        return out
     rc = lib().oracle_decode_thread(_ptr(st.words), len(st.words), _ptr(st.final), st.N,
                                     _ptr(_u32(st.f)), len(st.f), st.W, st.n, st.lgL, st.b,
                                     is_final, _ptr(idx), _ptr(y), q, lo, hi, _ptr(out),

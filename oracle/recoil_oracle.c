@@ -21,6 +21,8 @@
  *                                   cross-boundary phases)
  *   - split heuristic ............. Def. 4.1, Eq. 7
  *   - combining ................... Sec. 3.3 / 4.2 (drop metadata entries)
+ *   - adaptive coding ............. Sec. 3.1 (the PDF of every coding step is chosen
+ *                                   by the symbol index; here one row of a table set)
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   - Quantiser: f[s] = max(1, round_half_even(c[s] 2^n / N)) for present
@@ -129,29 +131,63 @@ static int find_symbol(const uint64_t *F, int A, uint64_t slot) {
     return lo;
 }
 
+/*
+ * The probability model: T quantised PDFs over one alphabet of A symbols.
+ * Symbol i is coded with PDF row tid[i] (adaptive coding keyed by the symbol
+ * index, Sec. 3.1), or with row 0 when tid is NULL (the static model).
+ */
+typedef struct {
+    const uint32_t *f;      /* T rows of A frequencies */
+    uint64_t *F;            /* T rows of A + 1 cumulative frequencies */
+    const uint32_t *tid;    /* row of every symbol index, or NULL */
+    int T, A;
+} oracle_model;
+
+/* Builds F; with check_sums, every row must sum to 2^n. */
+static int model_init(oracle_model *m, const uint32_t *f, int T, int A, const uint32_t *tid,
+                      int64_t N, int n, int check_sums) {
+    m->f = f;
+    m->tid = tid;
+    m->T = T;
+    m->A = A;
+    m->F = NULL;
+    if (T < 1 || A < 1) return OR_EINVAL;
+    if (tid)
+        for (int64_t i = 0; i < N; i++) if ((int64_t)tid[i] >= T) return OR_EINVAL;
+    m->F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)T * (size_t)(A + 1));
+    if (!m->F) return OR_ENOMEM;
+    for (int t = 0; t < T; t++) {
+        cdf_from_pdf(f + (size_t)t * A, A, m->F + (size_t)t * (A + 1));
+        if (check_sums && m->F[(size_t)t * (A + 1) + A] != ((uint64_t)1 << n)) {
+            free(m->F);
+            m->F = NULL;
+            return OR_EINVAL;
+        }
+    }
+    return OR_OK;
+}
+
+static int64_t row_of(const oracle_model *m, int64_t i) { return m->tid ? (int64_t)m->tid[i] : 0; }
+static const uint32_t *f_of(const oracle_model *m, int64_t i) { return m->f + row_of(m, i) * m->A; }
+static const uint64_t *F_of(const oracle_model *m, int64_t i) { return m->F + row_of(m, i) * (m->A + 1); }
+
 /* ------------------------------------------------------------------- encoder */
 
 /*
  * Interleaved rANS encoder (Eqs. 1 and 3, Sec. 2.2).
- * sym[0..N) are symbols, f the quantised PDF over A symbols.
+ * sym[0..N) are symbols coded with the model's PDF for their index.
  * Writes words B[0..), the final states xf[0..W), and for every word p the
  * renormalisation event that wrote it: ev_sym[p] = the symbol index whose
  * coding triggered it (the coder is ev_sym[p] mod W and the recorded index of
  * the state is ev_sym[p] - W), ev_y[p] = the coder state right after it.
  * cap is the capacity of B / ev_*. Returns the word count or a negative code.
  */
-int64_t oracle_encode(const uint32_t *sym, int64_t N, const uint32_t *f, int A,
-                      int W, int n, int lgL, int b,
-                      uint16_t *B, int64_t cap, uint32_t *xf,
-                      int64_t *ev_sym, uint32_t *ev_y) {
-    oracle_params P = {W, n, lgL, b};
-    if (!params_ok(&P) || N < 0) return OR_EINVAL;
-    uint64_t *F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(A + 1));
+static int64_t encode_model(const uint32_t *sym, int64_t N, const oracle_model *m,
+                            int W, int n, int lgL, int b,
+                            uint16_t *B, int64_t cap, uint32_t *xf,
+                            int64_t *ev_sym, uint32_t *ev_y) {
     uint64_t *x = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
-    if (!F || !x) { free(F); free(x); return OR_ENOMEM; }
-    cdf_from_pdf(f, A, F);
-    if (F[A] != ((uint64_t)1 << n)) { free(F); free(x); return OR_EINVAL; }
-
+    if (!x) return OR_ENOMEM;
     const uint64_t L = (uint64_t)1 << lgL;
     const uint64_t wmask = ((uint64_t)1 << b) - 1;
     for (int j = 0; j < W; j++) x[j] = L;
@@ -159,11 +195,12 @@ int64_t oracle_encode(const uint32_t *sym, int64_t N, const uint32_t *f, int A,
     for (int64_t i = 0; i < N; i++) {
         int j = (int)(i % W);
         uint32_t s = sym[i];
-        if ((int64_t)s >= A || f[s] == 0) { free(F); free(x); return OR_EINVAL; }
+        const uint32_t *f = f_of(m, i);
+        if ((int64_t)s >= m->A || f[s] == 0) { free(x); return OR_EINVAL; }
         uint64_t fs = f[s];
         /* Eq. 3: the state is renormalised against the f of the symbol about to be coded */
         while (x[j] >= ((L << b) >> n) * fs) {
-            if (p >= cap) { free(F); free(x); return OR_ENOMEM; }
+            if (p >= cap) { free(x); return OR_ENOMEM; }
             B[p] = (uint16_t)(x[j] & wmask);
             x[j] >>= b;
             ev_sym[p] = i;
@@ -171,12 +208,40 @@ int64_t oracle_encode(const uint32_t *sym, int64_t N, const uint32_t *f, int A,
             p++;
         }
         /* Eq. 1 */
-        x[j] = ((x[j] / fs) << n) + F[s] + (x[j] % fs);
+        x[j] = ((x[j] / fs) << n) + F_of(m, i)[s] + (x[j] % fs);
     }
     for (int j = 0; j < W; j++) xf[j] = (uint32_t)x[j];
-    free(F);
     free(x);
     return p;
+}
+
+int64_t oracle_encode(const uint32_t *sym, int64_t N, const uint32_t *f, int A,
+                      int W, int n, int lgL, int b,
+                      uint16_t *B, int64_t cap, uint32_t *xf,
+                      int64_t *ev_sym, uint32_t *ev_y) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || N < 0) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, 1, A, NULL, N, n, 1);
+    if (rc) return rc;
+    int64_t r = encode_model(sym, N, &m, W, n, lgL, b, B, cap, xf, ev_sym, ev_y);
+    free(m.F);
+    return r;
+}
+
+/* The same with T PDFs (rows of f, T x A) and a row per symbol index, tid[0..N). */
+int64_t oracle_encode_adaptive(const uint32_t *sym, int64_t N, const uint32_t *f, int T, int A,
+                               const uint32_t *tid, int W, int n, int lgL, int b,
+                               uint16_t *B, int64_t cap, uint32_t *xf,
+                               int64_t *ev_sym, uint32_t *ev_y) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || N < 0 || !tid) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, T, A, tid, N, n, 1);
+    if (rc) return rc;
+    int64_t r = encode_model(sym, N, &m, W, n, lgL, b, B, cap, xf, ev_sym, ev_y);
+    free(m.F);
+    return r;
 }
 
 /* -------------------------------------------------------------- serial decode */
@@ -188,16 +253,12 @@ int64_t oracle_encode(const uint32_t *sym, int64_t N, const uint32_t *f, int A,
  * word offset p at that moment. end_x[0..W) and *end_p receive the state at
  * the end (they should be L for every coder and -1).
  */
-int oracle_decode_serial(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
-                         const uint32_t *f, int A, int W, int n, int lgL, int b,
-                         uint32_t *out, uint32_t *end_x, int64_t *end_p,
-                         uint32_t *tr_x, int64_t *tr_p) {
-    oracle_params P = {W, n, lgL, b};
-    if (!params_ok(&P) || N < 0 || nw < 0) return OR_EINVAL;
-    uint64_t *F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(A + 1));
+static int decode_serial_model(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                               const oracle_model *m, int W, int n, int lgL, int b,
+                               uint32_t *out, uint32_t *end_x, int64_t *end_p,
+                               uint32_t *tr_x, int64_t *tr_p) {
     uint64_t *x = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
-    if (!F || !x) { free(F); free(x); return OR_ENOMEM; }
-    cdf_from_pdf(f, A, F);
+    if (!x) return OR_ENOMEM;
     const uint64_t L = (uint64_t)1 << lgL;
     const uint64_t mask = ((uint64_t)1 << n) - 1;
     for (int j = 0; j < W; j++) x[j] = xf[j];
@@ -205,8 +266,10 @@ int oracle_decode_serial(const uint16_t *B, int64_t nw, const uint32_t *xf, int6
     int rc = OR_OK;
     for (int64_t i = N - 1; i >= 0; i--) {
         int j = (int)(i % W);
+        const uint32_t *f = f_of(m, i);
+        const uint64_t *F = F_of(m, i);
         uint64_t slot = x[j] & mask;
-        int s = find_symbol(F, A, slot);
+        int s = find_symbol(F, m->A, slot);
         out[i] = (uint32_t)s;
         x[j] = f[s] * (x[j] >> n) - F[s] + slot;          /* Eq. 2 */
         if (tr_x) tr_x[i] = (uint32_t)x[j];
@@ -220,8 +283,35 @@ int oracle_decode_serial(const uint16_t *B, int64_t nw, const uint32_t *xf, int6
 done:
     if (end_x) for (int j = 0; j < W; j++) end_x[j] = (uint32_t)x[j];
     if (end_p) *end_p = p;
-    free(F);
     free(x);
+    return rc;
+}
+
+int oracle_decode_serial(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                         const uint32_t *f, int A, int W, int n, int lgL, int b,
+                         uint32_t *out, uint32_t *end_x, int64_t *end_p,
+                         uint32_t *tr_x, int64_t *tr_p) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || N < 0 || nw < 0) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, 1, A, NULL, N, n, 0);
+    if (rc) return rc;
+    rc = decode_serial_model(B, nw, xf, N, &m, W, n, lgL, b, out, end_x, end_p, tr_x, tr_p);
+    free(m.F);
+    return rc;
+}
+
+int oracle_decode_serial_adaptive(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                                  const uint32_t *f, int T, int A, const uint32_t *tid,
+                                  int W, int n, int lgL, int b,
+                                  uint32_t *out, uint32_t *end_x, int64_t *end_p) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || N < 0 || nw < 0 || !tid) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, T, A, tid, N, n, 1);
+    if (rc) return rc;
+    rc = decode_serial_model(B, nw, xf, N, &m, W, n, lgL, b, out, end_x, end_p, NULL, NULL);
+    free(m.F);
     return rc;
 }
 
@@ -322,18 +412,14 @@ int64_t oracle_combine(int64_t K, int64_t Mp, int64_t *keep) {
  * and trace_word the word read at that symbol's renormalisation (-1 if none;
  * the last one read if several). Returns OR_OK or a negative code.
  */
-int oracle_decode_thread(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
-                         const uint32_t *f, int A, int W, int n, int lgL, int b,
-                         int is_final, const int64_t *idx, const uint32_t *y, int64_t q,
-                         int64_t lo, int64_t hi, uint32_t *out,
-                         int8_t *trace, int64_t *trace_word) {
-    oracle_params P = {W, n, lgL, b};
-    if (!params_ok(&P)) return OR_EINVAL;
-    uint64_t *F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(A + 1));
+static int decode_thread_model(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                               const oracle_model *m, int W, int n, int lgL, int b,
+                               int is_final, const int64_t *idx, const uint32_t *y, int64_t q,
+                               int64_t lo, int64_t hi, uint32_t *out,
+                               int8_t *trace, int64_t *trace_word) {
     uint64_t *x = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
     char *init = (char *)malloc((size_t)W);
-    if (!F || !x || !init) { free(F); free(x); free(init); return OR_ENOMEM; }
-    cdf_from_pdf(f, A, F);
+    if (!x || !init) { free(x); free(init); return OR_ENOMEM; }
     const uint64_t L = (uint64_t)1 << lgL;
     const uint64_t mask = ((uint64_t)1 << n) - 1;
     int64_t p, start;
@@ -351,8 +437,10 @@ int oracle_decode_thread(const uint16_t *B, int64_t nw, const uint32_t *xf, int6
         int j = (int)(i % W);
         int8_t code;
         if (init[j]) {
+            const uint32_t *f = f_of(m, i);
+            const uint64_t *F = F_of(m, i);
             uint64_t slot = x[j] & mask;                     /* Eq. 2 */
-            int s = find_symbol(F, A, slot);
+            int s = find_symbol(F, m->A, slot);
             x[j] = f[s] * (x[j] >> n) - F[s] + slot;
             if (i <= hi) { out[i] = (uint32_t)s; code = TR_STORE; } else code = TR_DECODE;
         } else if (i == idx[j] + W) {
@@ -373,9 +461,24 @@ int oracle_decode_thread(const uint16_t *B, int64_t nw, const uint32_t *xf, int6
         if (trace) { trace[i] = code; trace_word[i] = wread; }
     }
 done:
-    free(F);
     free(x);
     free(init);
+    return rc;
+}
+
+int oracle_decode_thread(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                         const uint32_t *f, int A, int W, int n, int lgL, int b,
+                         int is_final, const int64_t *idx, const uint32_t *y, int64_t q,
+                         int64_t lo, int64_t hi, uint32_t *out,
+                         int8_t *trace, int64_t *trace_word) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P)) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, 1, A, NULL, N, n, 0);
+    if (rc) return rc;
+    rc = decode_thread_model(B, nw, xf, N, &m, W, n, lgL, b, is_final, idx, y, q, lo, hi, out,
+                             trace, trace_word);
+    free(m.F);
     return rc;
 }
 
@@ -385,22 +488,69 @@ done:
  * [m_{k-1}, m_k - 1] with m_k = min_j idx[k][j], m_{-1} = 0, and the final
  * thread owns up to N - 1. The threads run one after another.
  */
-int oracle_decode_splits(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
-                         const uint32_t *f, int A, int W, int n, int lgL, int b,
-                         int64_t K, const int64_t *idx, const uint32_t *y, const int64_t *q,
-                         uint32_t *out) {
+static int decode_splits_model(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                               const oracle_model *m, int W, int n, int lgL, int b,
+                               int64_t K, const int64_t *idx, const uint32_t *y, const int64_t *q,
+                               uint32_t *out) {
     if (K < 1) return OR_EINVAL;
     int64_t lo = 0;
     for (int64_t k = 0; k < K; k++) {
         int is_final = (k == K - 1);
-        int64_t m = is_final ? N : min_of(idx + k * W, W);
-        int64_t hi = m - 1;
-        if (m < lo) return OR_ECORRUPT;
-        int rc = oracle_decode_thread(B, nw, xf, N, f, A, W, n, lgL, b, is_final,
-                                      idx + k * W, y + k * W, is_final ? 0 : q[k],
-                                      lo, hi, out, NULL, NULL);
+        int64_t mk = is_final ? N : min_of(idx + k * W, W);
+        int64_t hi = mk - 1;
+        if (mk < lo) return OR_ECORRUPT;
+        int rc = decode_thread_model(B, nw, xf, N, m, W, n, lgL, b, is_final,
+                                     idx + k * W, y + k * W, is_final ? 0 : q[k],
+                                     lo, hi, out, NULL, NULL);
         if (rc) return rc;
-        lo = m;
+        lo = mk;
     }
     return OR_OK;
+}
+
+int oracle_decode_splits(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                         const uint32_t *f, int A, int W, int n, int lgL, int b,
+                         int64_t K, const int64_t *idx, const uint32_t *y, const int64_t *q,
+                         uint32_t *out) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P)) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, 1, A, NULL, N, n, 0);
+    if (rc) return rc;
+    rc = decode_splits_model(B, nw, xf, N, &m, W, n, lgL, b, K, idx, y, q, out);
+    free(m.F);
+    return rc;
+}
+
+/* Split decode with the adaptive model (T PDFs, row tid[i] for symbol i). */
+int oracle_decode_splits_adaptive(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                                  const uint32_t *f, int T, int A, const uint32_t *tid,
+                                  int W, int n, int lgL, int b,
+                                  int64_t K, const int64_t *idx, const uint32_t *y, const int64_t *q,
+                                  uint32_t *out) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || !tid) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, T, A, tid, N, n, 1);
+    if (rc) return rc;
+    rc = decode_splits_model(B, nw, xf, N, &m, W, n, lgL, b, K, idx, y, q, out);
+    free(m.F);
+    return rc;
+}
+
+/* One split decoder thread with the adaptive model (arguments as oracle_decode_thread). */
+int oracle_decode_thread_adaptive(const uint16_t *B, int64_t nw, const uint32_t *xf, int64_t N,
+                                  const uint32_t *f, int T, int A, const uint32_t *tid,
+                                  int W, int n, int lgL, int b,
+                                  int is_final, const int64_t *idx, const uint32_t *y, int64_t q,
+                                  int64_t lo, int64_t hi, uint32_t *out) {
+    oracle_params P = {W, n, lgL, b};
+    if (!params_ok(&P) || !tid) return OR_EINVAL;
+    oracle_model m;
+    int rc = model_init(&m, f, T, A, tid, N, n, 1);
+    if (rc) return rc;
+    rc = decode_thread_model(B, nw, xf, N, &m, W, n, lgL, b, is_final, idx, y, q, lo, hi, out,
+                             NULL, NULL);
+    free(m.F);
+    return rc;
 }

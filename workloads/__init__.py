@@ -24,6 +24,11 @@ Workloads (the paper's datasets are not available; these stand in for them):
 * ``gauss16``: clip(rint(Normal(mean, sigma)), 0, 4095) as uint16.
 * ``expbytes``: min(255, floor(Exp(scale = 256/lambda))), the reading used
   here for the paper's ``rand_lambda`` files (Sec. 5.1, Table 4).
+* ``adaptive``: latents of a hyperprior image codec (Sec. 3.1, 5.1): symbol i
+  has its own Gaussian scale, chosen by a per-index table number t_i, and is
+  clip(rint(A/2 + sigma_{t_i} Z), 0, A-1). The model (one quantised PDF per
+  scale) is an input too: it is built here from the Gaussian by the
+  largest-remainder rule, every symbol keeping at least one slot.
 """
 from __future__ import annotations
 
@@ -250,6 +255,78 @@ def batch_symbols(specs: list[Stream], threads: int | None = None) -> list[np.nd
     """Draw every stream of a batch; small streams are drawn in parallel."""
     with ThreadPoolExecutor(threads or _threads()) as ex:
         return list(ex.map(lambda s: s.symbols(threads=1), specs))
+
+
+# ------------------------------------------------------------------ adaptive model
+SCALE_MIN, SCALE_MAX = 0.11, 256.0      # Gaussian scales of the table set, log-spaced
+
+
+def scale_table(n_tables: int) -> np.ndarray:
+    return np.exp(np.linspace(math.log(SCALE_MIN), math.log(SCALE_MAX), n_tables))
+
+
+def gauss_freq_row(sigma: float, alphabet: int, n_bits: int) -> np.ndarray:
+    """Quantised PDF of clip(rint(A/2 + sigma Z), 0, A-1): 1 + floor(P * (2^n - A)) per symbol,
+    the slots left over going to the largest remainders (ties: smaller symbol)."""
+    pmf = gauss_pmf(alphabet // 2, sigma, alphabet)
+    spare = (1 << n_bits) - alphabet
+    if spare < 0:
+        raise ValueError("alphabet larger than 2^n")
+    raw = pmf * spare
+    f = 1 + np.floor(raw).astype(np.int64)
+    short = (1 << n_bits) - int(f.sum())
+    order = np.argsort(-(raw - np.floor(raw)), kind="stable")
+    f[order[:short]] += 1
+    return f.astype(np.uint32)
+
+
+@dataclass
+class AdaptiveStream:
+    """Symbols with a per-index distribution (adaptive coding keyed by the symbol index)."""
+    name: str
+    n_syms: int
+    n_bits: int = 16
+    sym_bytes: int = 2
+    n_tables: int = 64
+    alphabet: int = 256
+    seed: int = 8
+    index_mean: float = 20.0       # table numbers t_i ~ clip(rint(Normal(mean, sd)), 0, T-1)
+    index_sd: float = 12.0
+
+    def tables(self) -> np.ndarray:
+        """n_tables x alphabet quantised frequencies, each row summing to 2^n."""
+        return np.stack([gauss_freq_row(float(sg), self.alphabet, self.n_bits)
+                         for sg in scale_table(self.n_tables)])
+
+    def draw(self, threads: int | None = None) -> tuple[np.ndarray, np.ndarray]:
+        """(symbols, table numbers): deterministic in the seed, chunked like every other draw."""
+        n = self.n_syms
+        sym = np.empty(n, dtype=np.uint8 if self.sym_bytes == 1 else np.uint16)
+        tid = np.empty(n, dtype=np.uint8)
+        scales = scale_table(self.n_tables)
+        parts = _chunks(n)
+        kids = _seedseq(self.seed).spawn(max(1, len(parts)))
+
+        def fill(k):
+            s, m = parts[k]
+            g = np.random.Generator(np.random.PCG64(kids[k]))
+            t = np.clip(np.rint(g.normal(self.index_mean, self.index_sd, size=m)), 0, self.n_tables - 1)
+            tid[s:s + m] = t.astype(np.uint8)
+            v = np.rint(self.alphabet // 2 + scales[tid[s:s + m]] * g.standard_normal(size=m))
+            sym[s:s + m] = np.clip(v, 0, self.alphabet - 1).astype(sym.dtype)
+
+        if len(parts) <= 1:
+            for k in range(len(parts)):
+                fill(k)
+        else:
+            with ThreadPoolExecutor(threads or _threads()) as ex:
+                list(ex.map(fill, range(len(parts))))
+        return sym, tid
+
+
+def adaptive_256mib(n_syms: int = 1 << 27) -> AdaptiveStream:
+    """2^27 uint16 latents (256 MiB decoded), 64 Gaussian scale tables over 256 values, n = 16."""
+    return AdaptiveStream("adaptive", n_syms)
 
 
 def poisson_arrivals(rate_hz: float, count: int, seed: int = 7) -> np.ndarray:
