@@ -81,7 +81,9 @@ def lib():
 
 
 def _ptr(a: np.ndarray):
-    return C.c_void_p(a.ctypes.data) if a is not None else None
+    """Pointer argument for a C call; it holds a reference to the array, so a
+    temporary (e.g. a dtype conversion) lives until the call returns."""
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
 def _u32(a):
