@@ -55,7 +55,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="batch", choices=["batch", "single", "zipf", "serve", "conventional"])
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "single", "zipf", "serve", "conventional", "adaptive"])
     ap.add_argument("--dist", default="zipf", choices=["zipf", "skewed", "uniform", "gauss16", "laplace"],
                     help="single: which stream (zipf 1 GiB, the 256 MiB extremes, laplace 1 MiB)")
     ap.add_argument("--splits", type=int, default=9472, help="zipf: decoder split count")
@@ -368,6 +369,138 @@ def run_conventional(a):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_adaptive_rate(tables, n_bits, sym, tid, seconds: float, threads: int):
+    """Decoded GB/s of the oracle's adaptive serial decoder, one 16 Mi-symbol piece per host thread."""
+    import oracle
+    piece = 1 << 24
+    ks = list(range(0, len(sym), piece))
+
+    def enc(k):
+        return oracle.encode_adaptive(sym[k:k + piece], tid[k:k + piece], tables, n_bits)
+
+    done, wall, pos = 0, 0.0, 0
+    with ThreadPoolExecutor(threads) as ex:
+        while wall < seconds and pos < len(ks):
+            batch = ks[pos:pos + threads]
+            pos += len(batch)
+            codes = list(ex.map(enc, batch))
+
+            def dec(a):
+                k, (words, final, _, _) = a
+                out, _, end_p = oracle.decode_serial_adaptive(words, final, tid[k:k + piece], tables, n_bits)
+                return end_p == -1 and np.array_equal(out, sym[k:k + piece])
+
+            t = time.perf_counter()
+            ok = list(ex.map(dec, zip(batch, codes)))
+            wall += time.perf_counter() - t
+            assert all(ok)
+            done += sum(min(piece, len(sym) - k) for k in batch) * sym.itemsize
+    return done / wall / 1e9, done
+
+
+def run_adaptive(a):
+    """--workload adaptive: latents of a hyperprior image codec, each symbol with its own PDF (Sec. 3.1).
+
+    2^27 uint16 symbols (256 MiB decoded), 64 Gaussian scale tables over 256 values, n = 16 -- the
+    paper's image setting (16-bit symbols, a Gaussian per symbol, Sec. 5.1). Encoded at 65536 splits and
+    combined to --splits; the decoder reads one table-number byte per symbol, so the algorithmic bytes
+    are the words and the table numbers in plus the symbols out."""
+    import torch
+    import paper_2306_12141_b300 as R
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    st = workloads.adaptive_256mib(int((1 << 27) * a.scale))
+    tables = st.tables()
+    s, tid = st.draw()
+    enc = R.encode_adaptive(s, st.n_bits, tables, tid, max(1, min(65536, len(s) // 4096)))
+    warps = a.warps or 8
+    cs = torch.cuda.Stream(device=dev)
+    out = torch.empty(len(s) * 2, dtype=torch.uint8, device=dev)
+    ref = torch.from_numpy(s.view(np.uint8)).to(dev)
+    out_bytes = len(s) * 2
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            e0.record(cs)
+            fn()
+            e1.record(cs)
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    sweep = {}
+    with torch.cuda.stream(cs):
+        for k in a.sweep:
+            sp = R.Plan([R.combine_splits(enc, k)], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+            sws = torch.empty(sp.workspace_size, dtype=torch.uint8, device=dev)
+            sp.upload(sws, stream=cs)
+            t = timed(lambda: sp.decode([out.data_ptr()], cs), 5, 2)
+            assert sp.errors(cs) == 0 and torch.equal(out, ref)
+            sweep[str(k)] = round(out_bytes / (statistics.mean(t) * 1e-3) / 1e9, 1)
+            del sws
+        c = R.combine_splits(enc, a.splits)
+        plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+        ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
+        plan.upload(ws, stream=cs)
+        decode = lambda: plan.decode([out.data_ptr()], cs)  # noqa: E731
+        with Clocks(local) as clk:
+            t_end = time.time() + a.soak
+            while time.time() < t_end:
+                decode()
+                torch.cuda.synchronize()
+            ms = timed(decode, a.steps, a.warmup)
+        clocks = clk.summary()
+        clocks["note"] = f"sampled every 100 ms over a {a.soak:.1f} s soak of the same step and the timed steps"
+        assert plan.errors(cs) == 0, R.recoil_last_error()
+        assert torch.equal(out, ref)
+        launches = plan.launches
+        e2e = None
+        if not a.no_e2e:
+            R.stream_pin(c)
+            pipe = R.Pipeline([c], {"warps_per_cta": warps, "split_symbols": 0}, groups=1)
+            wsb, stb = pipe.sizes
+            pws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            stage = torch.empty(stb, dtype=torch.uint8, device=dev)
+            host = torch.empty(out_bytes, dtype=torch.uint8, pin_memory=True)
+            e_ms = timed(lambda: pipe.run([host.data_ptr()], pws, wsb, stage, stb, cs), max(3, a.steps // 2), 1)
+            assert pipe.errors() == 0 and np.array_equal(host.numpy(), s.view(np.uint8))
+            e2e = {"value": out_bytes / (statistics.mean(e_ms) * 1e-3) / 1e9, "unit": "GB/s",
+                   "h2d_bytes_per_step": int(2 * c.info["n_words"] + len(s)), "d2h_bytes_per_step": out_bytes,
+                   "ms_per_step": statistics.mean(e_ms),
+                   "note": "recoil_pipeline_run: H2D of words and table numbers, decode, D2H of the symbols "
+                           "(one group: no overlap inside a single stream)"}
+            del pws, stage
+    mean_ms = statistics.mean(ms)
+    in_bytes = 2 * c.info["n_words"] + 4 * 32 + len(s)
+    peaks = measured_peaks()
+    achieved = (out_bytes + in_bytes) / (mean_ms * 1e-3) / 1e9
+    line = {"metric": "decoded GB/s of an adaptive (per-symbol PDF) Recoil stream", "value": out_bytes / (mean_ms * 1e-3) / 1e9,
+            "unit": "GB/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": "adaptive: 2^27 uint16 latents, symbol i = clip(rint(128 + sigma_t Z)) with "
+                                   "t_i ~ clip(rint(N(20, 12)), 0, 63), 64 log-spaced Gaussian scale tables "
+                                   "(0.11..256) over 256 values, n=16, W=32",
+                       "splits": c.info["n_entries"], "warps_per_cta": warps, "symbols_bytes": out_bytes,
+                       "compressed_bytes": 2 * c.info["n_words"] + 4 * 32, "table_number_bytes": len(s),
+                       "l2": "inputs larger than L2 (no flush)", "scale": a.scale},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                         "kernel": "decode_kernel<kAdaptive16>",
+                         "bytes": "compressed words + table numbers in, symbols out"},
+            "clocks": clocks, "gpu_launches": launches * a.steps, "e2e": e2e, "split_sweep_gbs": sweep}
+    if not a.no_cpu:
+        threads = os.cpu_count() or 1
+        v, done = _oracle_adaptive_rate(tables, st.n_bits, s, tid, a.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{done / 1e6:.0f} MB of symbols in 16 Mi-symbol pieces, oracle adaptive "
+                                          f"serial decoder (plain C -O2), one piece per host thread"}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(a):
     import torch
     import paper_2306_12141_b300 as R
@@ -580,6 +713,8 @@ if __name__ == "__main__":
         run_reference(args)
     elif args.workload == "conventional":
         run_conventional(args)
+    elif args.workload == "adaptive":
+        run_adaptive(args)
     elif args.workload == "serve":
         if args.serve_requests == 5000:
             args.serve_requests = 20000

@@ -63,10 +63,12 @@ typedef struct {
   uint32_t n_entries;         /* split entries, including the final-state entry */
   uint32_t n_bits;
   uint32_t sym_bytes;
-  uint32_t alphabet;          /* entries of the frequency table */
+  uint32_t alphabet;          /* symbols of the (each) frequency table */
   uint64_t bitstream_bytes;   /* 2 * n_words + 4 * W (final states) */
   uint64_t metadata_bytes;    /* unpacked split metadata: (8 + 2W + 4W) bytes per regular entry */
   uint64_t max_sync;          /* largest synchronisation section, in symbols (Sec. 4.1) */
+  uint32_t n_tables;          /* adaptive model: PDF rows (0: one static PDF) */
+  uint32_t reserved;
 } recoil_info;
 
 /*
@@ -105,12 +107,36 @@ int recoil_encode_with_table(const void* syms, uint64_t n_syms, const recoil_par
  */
 int recoil_combine_splits(const recoil_stream* in, uint32_t target_splits, recoil_stream** out);
 
+/*
+ * Adaptive coding (Sec. 3.1): the PDF of every coding step is chosen by the
+ * symbol index, as in hyperprior image codecs. Symbol i is coded with row
+ * table_index[i] of a set of quantised PDFs; the decoder reads the same table
+ * numbers (the codec derives them before entropy decoding), so the stream
+ * keeps a copy of them and the decoder tables hold every row.
+ *   freq         n_tables * alphabet frequencies, row t = PDF t over the
+ *                alphabet; every row sums to 2^n and gives every symbol a
+ *                frequency >= 1 (a hyperprior codec's discretised densities
+ *                do); so 2 <= alphabet <= 2^n
+ *   n_tables     rows, 1..256; table_index holds n_syms bytes, each < n_tables
+ *   alphabet     <= 4096 (256 for 8-bit symbols); the n_tables CDF rows must
+ *                fit in shared memory with the decoder rings
+ *                (n_tables * (alphabet + 1) * 2 bytes, rounded up, <= ~160 KiB)
+ * Split placement, combining and plans work as for static streams; adaptive
+ * streams decode with 4, 8 or 16 warps per CTA, are not serialised
+ * (recoil_serialize) and not taken by recoil_decode_noalloc.
+ * Errors: EINVAL (bad parameters, a row that does not sum to 2^n or has a zero,
+ * a table number or symbol out of range), ENOMEM.
+ */
+int recoil_encode_adaptive(const void* syms, uint64_t n_syms, const recoil_params* params, const uint32_t* freq,
+                           uint32_t n_tables, uint32_t alphabet, const uint8_t* table_index, uint32_t max_splits,
+                           recoil_stream** out);
+
 /* Sizes and counts of a stream. Errors: EINVAL. */
 int recoil_stream_info(const recoil_stream* s, recoil_info* out);
 
 /*
  * Copy a stream's parts out (any pointer may be NULL to skip it):
- *   freq[alphabet], words[n_words], final_states[W],
+ *   freq[alphabet] (adaptive: [n_tables * alphabet]), words[n_words], final_states[W],
  *   entry_word[R], entry_index[R*W] (recorded symbol index per coder),
  *   entry_state[R*W] (16-bit states), R = n_entries - 1 regular entries.
  */
@@ -160,7 +186,8 @@ int recoil_stream_pin(recoil_stream* s);
  *   be NULL) = the packed metadata section's size. Errors: EINVAL (null, or a
  *   group difference wider than 16 bits / an offset wider than 32 bits).
  * recoil_serialize: writes the container into buf (cap bytes; ENOMEM if too
- *   small) and its size into *written. Errors: EINVAL, ENOMEM.
+ *   small) and its size into *written. Errors: EINVAL (also for an adaptive
+ *   stream, whose model and table numbers travel with the codec), ENOMEM.
  * recoil_deserialize: parses size bytes at buf into a new stream (freed with
  *   recoil_free), validated as recoil_stream_import does. Errors: EINVAL
  *   (null), ECORRUPT (bad magic, truncated or inconsistent data), ENOMEM.
@@ -410,8 +437,9 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
  * calls whose GPU work overlaps (several host threads or CUDA streams) race on
  * it and must not be made. Allocates nothing on the device (host memory only
  * for building the descriptors). Returns after the decode has finished on
- * cuda_stream. Errors: EINVAL (null, small or misaligned d_words, or a stream
- * whose descriptors and tables exceed the array: combine it to fewer splits),
+ * cuda_stream. Errors: EINVAL (null, small or misaligned d_words, an adaptive
+ * stream, or a stream whose descriptors and tables exceed the array: combine
+ * it to fewer splits),
  * ECORRUPT (the decoder found an inconsistent stream), ECUDA.
  */
 int recoil_decode_noalloc(const recoil_stream* stream, const void* d_words, size_t words_bytes, void* d_out,

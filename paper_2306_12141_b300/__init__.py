@@ -35,7 +35,8 @@ class Params(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_syms", C.c_uint64), ("n_words", C.c_uint64), ("n_entries", C.c_uint32),
                 ("n_bits", C.c_uint32), ("sym_bytes", C.c_uint32), ("alphabet", C.c_uint32),
-                ("bitstream_bytes", C.c_uint64), ("metadata_bytes", C.c_uint64), ("max_sync", C.c_uint64)]
+                ("bitstream_bytes", C.c_uint64), ("metadata_bytes", C.c_uint64), ("max_sync", C.c_uint64),
+                ("n_tables", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class BatchOpts(C.Structure):
@@ -78,7 +79,7 @@ EXPORTS = [
     "recoil_autotune_workspace_size", "recoil_serve", "recoil_serve_arena_size",
     "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
     "recoil_pipeline_free", "recoil_shard", "recoil_encode_with_table",
-    "recoil_serialized_size", "recoil_serialize", "recoil_deserialize",
+    "recoil_serialized_size", "recoil_serialize", "recoil_deserialize", "recoil_encode_adaptive",
 ]
 
 _lib = None
@@ -96,6 +97,7 @@ def lib():
         L.recoil_encode_with_splits.argtypes = [vp, u64, C.POINTER(Params), u32, pp]
         L.recoil_combine_splits.argtypes = [vp, u32, pp]
         L.recoil_encode_with_table.argtypes = [vp, u64, C.POINTER(Params), vp, u32, u32, pp]
+        L.recoil_encode_adaptive.argtypes = [vp, u64, C.POINTER(Params), vp, u32, u32, vp, u32, pp]
         L.recoil_stream_info.argtypes = [vp, C.POINTER(Info)]
         L.recoil_stream_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.recoil_stream_import.argtypes = [C.POINTER(Params), u64, u32, vp, vp, u64, vp, u32, vp, vp, vp, pp]
@@ -212,6 +214,22 @@ def recoil_encode_with_table(symbols: np.ndarray, n_bits: int, freq, max_splits:
     return Stream(h.value)
 
 
+def recoil_encode_adaptive(symbols: np.ndarray, n_bits: int, tables, table_index, max_splits: int) -> Stream:
+    """Adaptive coding (Sec. 3.1): symbol i coded with PDF row table_index[i] of tables (T x A)."""
+    s = np.ascontiguousarray(symbols)
+    if s.dtype not in (np.uint8, np.uint16):
+        raise TypeError("symbols must be uint8 or uint16")
+    f = np.ascontiguousarray(np.atleast_2d(tables), dtype=np.uint32)
+    t = np.ascontiguousarray(table_index, dtype=np.uint8)
+    if t.shape != s.shape:
+        raise ValueError("one table number per symbol")
+    p = Params(n_bits, s.dtype.itemsize)
+    h = C.c_void_p()
+    _check(lib().recoil_encode_adaptive(s.ctypes.data if s.size else None, s.size, C.byref(p), _ptr(f), f.shape[0],
+                                        f.shape[1], t.ctypes.data if t.size else None, max_splits, C.byref(h)))
+    return Stream(h.value)
+
+
 def recoil_combine_splits(stream: Stream, target_splits: int) -> Stream:
     h = C.c_void_p()
     _check(lib().recoil_combine_splits(stream.handle, target_splits, C.byref(h)))
@@ -228,7 +246,7 @@ def recoil_stream_export(stream: Stream) -> dict:
     info = recoil_stream_info(stream)
     R = info["n_entries"] - 1
     out = {
-        "freq": np.zeros(info["alphabet"], dtype=np.uint32),
+        "freq": np.zeros(max(1, info["n_tables"]) * info["alphabet"], dtype=np.uint32),
         "words": np.zeros(info["n_words"], dtype=np.uint16),
         "final": np.zeros(W, dtype=np.uint32),
         "entry_word": np.zeros(R, dtype=np.uint64),
@@ -242,10 +260,11 @@ def recoil_stream_export(stream: Stream) -> dict:
 
 
 def stream_freq(stream: Stream) -> np.ndarray:
-    """The stream's quantised PDF only (recoil_stream_export with every other part skipped)."""
-    f = np.zeros(stream_info(stream)["alphabet"], dtype=np.uint32)
+    """The stream's quantised PDF only (adaptive: n_tables x alphabet), via recoil_stream_export."""
+    info = stream_info(stream)
+    f = np.zeros(max(1, info["n_tables"]) * info["alphabet"], dtype=np.uint32)
     _check(lib().recoil_stream_export(stream.handle, _ptr(f), None, None, None, None, None))
-    return f
+    return f.reshape(info["n_tables"], info["alphabet"]) if info["n_tables"] else f
 
 
 def recoil_stream_import(n_bits: int, sym_bytes: int, n_syms: int, freq, words, final,
@@ -535,6 +554,7 @@ def recoil_decode_noalloc(stream: Stream, d_words, words_bytes: int, d_out, cuda
 encode_with_splits = recoil_encode_with_splits
 combine_splits = recoil_combine_splits
 encode_with_table = recoil_encode_with_table
+encode_adaptive = recoil_encode_adaptive
 stream_info = recoil_stream_info
 stream_export = recoil_stream_export
 stream_import = recoil_stream_import

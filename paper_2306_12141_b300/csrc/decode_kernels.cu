@@ -80,12 +80,65 @@ struct Tables {
   }
 };
 
+// Adaptive model (Sec. 3.1): symbol i is coded with PDF row tid[i]. Row t
+// holds F(0..A) of PDF t as 16-bit values (F(A) = 2^n modulo 2^16). The
+// symbol is the last s with F(s) <= slot, found by DEPTH halvings
+// (2^DEPTH >= A, probes at or beyond A skipped); f = F(s+1) - F(s) modulo
+// 2^16, exact since every f of an adaptive model is below 2^16.
+template <uint32_t KIND, int DEPTH>
+struct AdaptiveTables {
+  const uint16_t* cdf;
+  uint32_t stride, A;
+  __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream& st) {
+    cdf = reinterpret_cast<const uint16_t*>(smem);
+    stride = st.row_stride;
+    A = st.alphabet;
+  }
+  __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask, uint32_t t) const {
+    const uint32_t slot = x & mask;
+    const uint16_t* row = cdf + t * stride;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = DEPTH - 1; k >= 0; --k) {
+      const uint32_t m = s | (1u << k);
+      if (m < A && row[m] <= slot) s = m;
+    }
+    const uint32_t F0 = row[s];
+    const uint32_t f = (uint32_t)(uint16_t)(row[s + 1] - F0);
+    x = f * (x >> n) + slot - F0;
+    return s;
+  }
+};
+
+template <uint32_t KIND>
+__host__ __device__ constexpr bool is_adaptive() {
+  return KIND == kAdaptive8 || KIND == kAdaptive16;
+}
+
+// Decoder tables of a kind (DEPTH only matters to adaptive kinds).
+template <uint32_t KIND, int DEPTH>
+struct TablesOf {
+  using T = Tables<KIND>;
+};
+template <int DEPTH>
+struct TablesOf<kAdaptive8, DEPTH> {
+  using T = AdaptiveTables<kAdaptive8, DEPTH>;
+};
+template <int DEPTH>
+struct TablesOf<kAdaptive16, DEPTH> {
+  using T = AdaptiveTables<kAdaptive16, DEPTH>;
+};
+
 template <uint32_t KIND>
 struct SymOut {
   using T = uint8_t;
 };
 template <>
 struct SymOut<kGeneric16> {
+  using T = uint16_t;
+};
+template <>
+struct SymOut<kAdaptive16> {
   using T = uint16_t;
 };
 
@@ -122,14 +175,23 @@ struct Walker {
   uint4 pre;           // prefetched chunk (cbase/256 - 2)
 };
 
-template <uint32_t KIND>
+template <uint32_t KIND, int DEPTH>
 struct EntryDecoder {
-  Tables<KIND> T;
+  typename TablesOf<KIND, DEPTH>::T T;
   const uint16_t* __restrict__ words;
+  const uint8_t* __restrict__ tid;     // adaptive kinds: PDF row of every symbol index
   uint16_t* ring;
   typename SymOut<KIND>::T* __restrict__ out;
   uint32_t n, mask, gt;
   int lane;
+
+  // Eq. 2 for symbol i (the table row is the symbol's own under an adaptive model)
+  __device__ __forceinline__ uint32_t dec(uint32_t& x, int i) const {
+    if constexpr (is_adaptive<KIND>())
+      return T.step(x, n, mask, __ldg(tid + i));
+    else
+      return T.step(x, n, mask);
+  }
 
   __device__ __forceinline__ void refill(Walker& w) {
     __syncwarp();
@@ -170,7 +232,7 @@ struct EntryDecoder {
     const bool dec = (g < act) && (i >= lo);
     const bool join = (g == act);
     if (dec) {
-      const uint32_t s = T.step(w.x, n, mask);
+      const uint32_t s = this->dec(w.x, i);
       if (i < hi1) out[i] = (typename SymOut<KIND>::T)s;
     }
     if (join) w.x = x0;
@@ -180,9 +242,9 @@ struct EntryDecoder {
     settle(w, rp0);
   }
 
-  // A group step where every coder decodes and every symbol is owned.
-  __device__ __forceinline__ void sstep(Walker& w, typename SymOut<KIND>::T* o) {
-    const uint32_t s = T.step(w.x, n, mask);
+  // A group step where every coder decodes and every symbol is owned (i: its index).
+  __device__ __forceinline__ void sstep(Walker& w, typename SymOut<KIND>::T* o, int i) {
+    const uint32_t s = dec(w.x, i);
     *o = (typename SymOut<KIND>::T)s;
     renorm(w, w.x < kL);
   }
@@ -230,15 +292,16 @@ struct EntryDecoder {
       // block, every read stays inside the two staged chunks
       while (g - 7 >= steady_lo) {
         const int rp0 = w.rp;
+        const int i0 = g * kW + lane;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sstep(w, o - u * kW);
+        for (int u = 0; u < 8; ++u) sstep(w, o - u * kW, i0 - u * kW);
         o -= 8 * kW;
         g -= 8;
         settle(w, rp0);
       }
       for (; g >= steady_lo; --g) {
         const int rp0 = w.rp;
-        sstep(w, o);
+        sstep(w, o, g * kW + lane);
         o -= kW;
         settle(w, rp0);
       }
@@ -274,14 +337,19 @@ struct EntryDecoder {
 #ifndef RECOIL_RESIDENT_WARPS
 #define RECOIL_RESIDENT_WARPS 48
 #endif
-template <int WARPS>
+// The adaptive step needs more registers (the CDF search): 32 warps per SM.
+#ifndef RECOIL_RESIDENT_WARPS_ADAPTIVE
+#define RECOIL_RESIDENT_WARPS_ADAPTIVE 32
+#endif
+template <uint32_t KIND, int WARPS>
 struct Residency {
-  static constexpr int kWant = RECOIL_RESIDENT_WARPS / WARPS;
+  static constexpr int kWarps = is_adaptive<KIND>() ? RECOIL_RESIDENT_WARPS_ADAPTIVE : RECOIL_RESIDENT_WARPS;
+  static constexpr int kWant = kWarps / WARPS;
   static constexpr int kMinBlocks = kWant < 1 ? 1 : (kWant > 32 ? 32 : kWant);
 };
 
-template <uint32_t KIND, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, Residency<WARPS>::kMinBlocks) decode_kernel(const LaunchArgs a) {
+template <uint32_t KIND, int WARPS, int DEPTH>
+__global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlocks)) decode_kernel(const LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item;
   const int warp = threadIdx.x >> 5;
@@ -309,9 +377,10 @@ __global__ void __launch_bounds__(WARPS * 32, Residency<WARPS>::kMinBlocks) deco
       // the entry's own stream: an item may span streams that share one table
       const DevEntry* ent = a.entries + item.entry + warp;
       const uint32_t sid = ent->stream;
-      EntryDecoder<KIND> d;
+      EntryDecoder<KIND, DEPTH> d;
       d.T.bind(smem, st);
       d.words = a.word_pool + a.streams[sid].words;
+      d.tid = reinterpret_cast<const uint8_t*>(a.word_pool + a.streams[sid].tid);
       d.ring = ring;
       d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[sid]);
       d.n = st.n_bits;
@@ -329,45 +398,91 @@ size_t smem_bytes(uint32_t warps, uint32_t table_smem) {
   return (size_t)table_smem + (size_t)warps * kRingSlots * sizeof(uint16_t);
 }
 
-template <uint32_t KIND, int WARPS>
-cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+template <uint32_t KIND, int WARPS, int DEPTH>
+cudaError_t launch_kwd(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   const size_t sm = smem_bytes(WARPS, a.table_smem);
-  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS, DEPTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  decode_kernel<KIND, WARPS><<<grid, WARPS * 32, sm, s>>>(a);
+  decode_kernel<KIND, WARPS, DEPTH><<<grid, WARPS * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-template <uint32_t KIND, int WARPS>
-int occupancy_kw(uint32_t table_smem, int* out) {
+template <uint32_t KIND, int WARPS, int DEPTH>
+int occupancy_kwd(uint32_t table_smem, int* out) {
   const size_t sm = smem_bytes(WARPS, table_smem);
-  if (cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+  if (cudaFuncSetAttribute(decode_kernel<KIND, WARPS, DEPTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return -1;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS, DEPTH>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
+}
+
+// Static kinds come in every CTA size; adaptive kinds in 4, 8 and 16 warps
+// and three search depths (alphabets up to 16, 256 and 4096 symbols).
+template <uint32_t KIND, int WARPS>
+cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  if constexpr (is_adaptive<KIND>()) {
+    switch (a.depth) {
+      case 4: return launch_kwd<KIND, WARPS, 4>(a, grid, s);
+      case 8: return launch_kwd<KIND, WARPS, 8>(a, grid, s);
+      case 12: return launch_kwd<KIND, WARPS, 12>(a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+  } else {
+    return launch_kwd<KIND, WARPS, 0>(a, grid, s);
+  }
+}
+
+template <uint32_t KIND, int WARPS>
+int occupancy_kw(uint32_t depth, uint32_t table_smem, int* out) {
+  if constexpr (is_adaptive<KIND>()) {
+    switch (depth) {
+      case 4: return occupancy_kwd<KIND, WARPS, 4>(table_smem, out);
+      case 8: return occupancy_kwd<KIND, WARPS, 8>(table_smem, out);
+      case 12: return occupancy_kwd<KIND, WARPS, 12>(table_smem, out);
+    }
+    return -1;
+  } else {
+    return occupancy_kwd<KIND, WARPS, 0>(table_smem, out);
+  }
 }
 
 template <uint32_t KIND>
 cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  switch (a.warps) {
-    case 1: return launch_kw<KIND, 1>(a, grid, s);
-    case 2: return launch_kw<KIND, 2>(a, grid, s);
-    case 4: return launch_kw<KIND, 4>(a, grid, s);
-    case 8: return launch_kw<KIND, 8>(a, grid, s);
-    case 16: return launch_kw<KIND, 16>(a, grid, s);
-    case 32: return launch_kw<KIND, 32>(a, grid, s);
+  if constexpr (is_adaptive<KIND>()) {
+    switch (a.warps) {
+      case 4: return launch_kw<KIND, 4>(a, grid, s);
+      case 8: return launch_kw<KIND, 8>(a, grid, s);
+      case 16: return launch_kw<KIND, 16>(a, grid, s);
+    }
+  } else {
+    switch (a.warps) {
+      case 1: return launch_kw<KIND, 1>(a, grid, s);
+      case 2: return launch_kw<KIND, 2>(a, grid, s);
+      case 4: return launch_kw<KIND, 4>(a, grid, s);
+      case 8: return launch_kw<KIND, 8>(a, grid, s);
+      case 16: return launch_kw<KIND, 16>(a, grid, s);
+      case 32: return launch_kw<KIND, 32>(a, grid, s);
+    }
   }
   return cudaErrorInvalidValue;
 }
 
 template <uint32_t KIND>
-int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
-  switch (warps) {
-    case 1: return occupancy_kw<KIND, 1>(table_smem, out);
-    case 2: return occupancy_kw<KIND, 2>(table_smem, out);
-    case 4: return occupancy_kw<KIND, 4>(table_smem, out);
-    case 8: return occupancy_kw<KIND, 8>(table_smem, out);
-    case 16: return occupancy_kw<KIND, 16>(table_smem, out);
-    case 32: return occupancy_kw<KIND, 32>(table_smem, out);
+int occupancy_k(uint32_t warps, uint32_t depth, uint32_t table_smem, int* out) {
+  if constexpr (is_adaptive<KIND>()) {
+    switch (warps) {
+      case 4: return occupancy_kw<KIND, 4>(depth, table_smem, out);
+      case 8: return occupancy_kw<KIND, 8>(depth, table_smem, out);
+      case 16: return occupancy_kw<KIND, 16>(depth, table_smem, out);
+    }
+  } else {
+    switch (warps) {
+      case 1: return occupancy_kw<KIND, 1>(depth, table_smem, out);
+      case 2: return occupancy_kw<KIND, 2>(depth, table_smem, out);
+      case 4: return occupancy_kw<KIND, 4>(depth, table_smem, out);
+      case 8: return occupancy_kw<KIND, 8>(depth, table_smem, out);
+      case 16: return occupancy_kw<KIND, 16>(depth, table_smem, out);
+      case 32: return occupancy_kw<KIND, 32>(depth, table_smem, out);
+    }
   }
   return -1;
 }
@@ -376,20 +491,32 @@ int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
 
 bool warps_supported(uint32_t w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32; }
 
+bool adaptive_warps_supported(uint32_t w) { return w == 4 || w == 8 || w == 16; }
+
+uint32_t adaptive_depth_class(uint32_t alphabet) {
+  if (alphabet <= 16) return 4;
+  if (alphabet <= 256) return 8;
+  return alphabet <= kMaxAdaptiveAlphabet ? 12 : 0;
+}
+
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   switch (kind) {
     case kPacked8: return launch_k<kPacked8>(a, grid, s);
     case kGeneric8: return launch_k<kGeneric8>(a, grid, s);
     case kGeneric16: return launch_k<kGeneric16>(a, grid, s);
+    case kAdaptive8: return launch_k<kAdaptive8>(a, grid, s);
+    case kAdaptive16: return launch_k<kAdaptive16>(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out) {
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t depth, uint32_t table_smem, int* out) {
   switch (kind) {
-    case kPacked8: return occupancy_k<kPacked8>(warps, table_smem, out);
-    case kGeneric8: return occupancy_k<kGeneric8>(warps, table_smem, out);
-    case kGeneric16: return occupancy_k<kGeneric16>(warps, table_smem, out);
+    case kPacked8: return occupancy_k<kPacked8>(warps, depth, table_smem, out);
+    case kGeneric8: return occupancy_k<kGeneric8>(warps, depth, table_smem, out);
+    case kGeneric16: return occupancy_k<kGeneric16>(warps, depth, table_smem, out);
+    case kAdaptive8: return occupancy_k<kAdaptive8>(warps, depth, table_smem, out);
+    case kAdaptive16: return occupancy_k<kAdaptive16>(warps, depth, table_smem, out);
   }
   return -1;
 }

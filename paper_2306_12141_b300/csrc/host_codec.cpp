@@ -50,6 +50,7 @@ int fail(int code, const std::string& msg) {
 void clear_error() { g_last_error.clear(); }
 
 bool Stream::constant() const {
+  if (adaptive()) return false;
   for (uint32_t f : freq)
     if (f == (1u << n_bits)) return true;
   return false;
@@ -106,9 +107,11 @@ struct Records {
   std::vector<uint16_t> y;
 };
 
-template <typename T>
-void encode_loop(const T* syms, uint64_t N, const std::vector<EncSym>& tab, uint32_t n,
-                 std::vector<uint16_t>& words, Records& rec, uint32_t* final_x) {
+// tab holds one EncSym per symbol of each PDF row; with a table-number array
+// (adaptive model, Sec. 3.1) symbol i uses row tid[i], else row 0.
+template <typename T, bool ADAPTIVE>
+void encode_loop(const T* syms, uint64_t N, const std::vector<EncSym>& tab, uint32_t A, const uint8_t* tid,
+                 uint32_t n, std::vector<uint16_t>& words, Records& rec, uint32_t* final_x) {
   uint32_t x[kW];
   for (int j = 0; j < kW; j++) x[j] = kL;
   uint16_t* wp = words.data();
@@ -117,7 +120,7 @@ void encode_loop(const T* syms, uint64_t N, const std::vector<EncSym>& tab, uint
   uint64_t p = 0;
   for (uint64_t i = 0; i < N; i++) {
     const int j = (int)(i & (kW - 1));
-    const EncSym& e = tab[syms[i]];
+    const EncSym& e = ADAPTIVE ? tab[(size_t)tid[i] * A + syms[i]] : tab[syms[i]];
     uint32_t v = x[j];
     if (v > e.xmax) {                        // Eq. 3: one step suffices since b >= n
       wp[p] = (uint16_t)v;
@@ -242,19 +245,24 @@ const char* recoil_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
 
-// Encode with a given quantised PDF (validated by the callers), place splits.
+// Encode with given quantised PDFs (validated by the callers), place splits.
+// n_tables == 0: one static PDF; else freq holds n_tables rows and tid the
+// row of every symbol.
 static int encode_common(const void* syms, uint64_t n_syms, const recoil_params* params, std::vector<uint32_t> freq,
-                         uint32_t max_splits, recoil_stream** out) {
+                         uint32_t n_tables, const uint8_t* tid, uint32_t max_splits, recoil_stream** out) {
   try {
     std::unique_ptr<recoil_stream> s(new recoil_stream());
     s->n_bits = params->n_bits;
     s->sym_bytes = params->sym_bytes;
     s->n_syms = n_syms;
     s->freq = std::move(freq);
-    const uint32_t n = params->n_bits;
+    s->n_tables = n_tables;
+    if (n_tables) s->tid = std::make_shared<const std::vector<uint8_t>>(tid, tid + n_syms);
+    const uint32_t n = params->n_bits, A = s->alphabet();
     std::vector<EncSym> tab(s->freq.size());
     uint32_t F = 0;
     for (size_t k = 0; k < tab.size(); k++) {
+      if (k % A == 0) F = 0;                               // each row is its own CDF
       const uint32_t f = s->freq[k];
       tab[k].f = f;
       tab[k].F = F;
@@ -268,10 +276,14 @@ static int encode_common(const void* syms, uint64_t n_syms, const recoil_params*
     Records rec;
     rec.sym.resize(n_syms + 1);
     rec.y.resize(n_syms + 1);
-    if (params->sym_bytes == 1)
-      encode_loop((const uint8_t*)syms, n_syms, tab, n, *words, rec, s->final_x);
-    else
-      encode_loop((const uint16_t*)syms, n_syms, tab, n, *words, rec, s->final_x);
+    const uint8_t* t = n_tables ? s->tid->data() : nullptr;
+    if (params->sym_bytes == 1) {
+      if (n_tables) encode_loop<uint8_t, true>((const uint8_t*)syms, n_syms, tab, A, t, n, *words, rec, s->final_x);
+      else encode_loop<uint8_t, false>((const uint8_t*)syms, n_syms, tab, A, t, n, *words, rec, s->final_x);
+    } else {
+      if (n_tables) encode_loop<uint16_t, true>((const uint16_t*)syms, n_syms, tab, A, t, n, *words, rec, s->final_x);
+      else encode_loop<uint16_t, false>((const uint16_t*)syms, n_syms, tab, A, t, n, *words, rec, s->final_x);
+    }
     words->shrink_to_fit();
     std::vector<uint64_t> qs;
     place_splits(rec, n_syms, max_splits, qs);
@@ -309,7 +321,7 @@ int recoil_encode_with_splits(const void* syms, uint64_t n_syms, const recoil_pa
     return fail(RECOIL_ENOMEM, "host allocation failed");
   }
   if (rc) return rc;
-  return encode_common(syms, n_syms, params, std::move(freq), std::max<uint32_t>(max_splits, 1), out);
+  return encode_common(syms, n_syms, params, std::move(freq), 0, nullptr, std::max<uint32_t>(max_splits, 1), out);
 }
 
 int recoil_encode_with_table(const void* syms, uint64_t n_syms, const recoil_params* params, const uint32_t* freq,
@@ -326,8 +338,37 @@ int recoil_encode_with_table(const void* syms, uint64_t n_syms, const recoil_par
     const uint32_t v = params->sym_bytes == 1 ? ((const uint8_t*)syms)[i] : ((const uint16_t*)syms)[i];
     if (v >= alphabet || !freq[v]) return fail(RECOIL_EINVAL, "a symbol has no probability in the table");
   }
-  return encode_common(syms, n_syms, params, std::vector<uint32_t>(freq, freq + alphabet),
+  return encode_common(syms, n_syms, params, std::vector<uint32_t>(freq, freq + alphabet), 0, nullptr,
                        std::max<uint32_t>(max_splits, 1), out);
+}
+
+int recoil_encode_adaptive(const void* syms, uint64_t n_syms, const recoil_params* params, const uint32_t* freq,
+                           uint32_t n_tables, uint32_t alphabet, const uint8_t* table_index, uint32_t max_splits,
+                           recoil_stream** out) {
+  clear_error();
+  int rc = check_params(syms, n_syms, params, out);
+  if (rc) return rc;
+  if (!freq || (!table_index && n_syms)) return fail(RECOIL_EINVAL, "null argument");
+  if (n_tables < 1 || n_tables > kMaxTables) return fail(RECOIL_EINVAL, "n_tables must be in [1, 256]");
+  const uint32_t amax = std::min<uint32_t>(params->sym_bytes == 1 ? 256u : kMaxAdaptiveAlphabet, 1u << params->n_bits);
+  if (alphabet < 2 || alphabet > amax)
+    return fail(RECOIL_EINVAL, "alphabet must be in [2, min(2^n, 4096)] (256 for 8-bit symbols)");
+  for (uint32_t t = 0; t < n_tables; t++) {
+    uint64_t sum = 0;
+    for (uint32_t k = 0; k < alphabet; k++) {
+      const uint32_t f = freq[(size_t)t * alphabet + k];
+      if (f == 0) return fail(RECOIL_EINVAL, "an adaptive PDF row gives a symbol no probability");
+      sum += f;
+    }
+    if (sum != (1ull << params->n_bits)) return fail(RECOIL_EINVAL, "every PDF row must sum to 2^n");
+  }
+  for (uint64_t i = 0; i < n_syms; i++) {
+    const uint32_t v = params->sym_bytes == 1 ? ((const uint8_t*)syms)[i] : ((const uint16_t*)syms)[i];
+    if (v >= alphabet) return fail(RECOIL_EINVAL, "a symbol lies outside the alphabet");
+    if (table_index[i] >= n_tables) return fail(RECOIL_EINVAL, "a table number is not below n_tables");
+  }
+  return encode_common(syms, n_syms, params, std::vector<uint32_t>(freq, freq + (size_t)n_tables * alphabet),
+                       n_tables, table_index, std::max<uint32_t>(max_splits, 1), out);
 }
 
 int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_stream** out) {
@@ -341,6 +382,8 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_strea
     s->sym_bytes = in->sym_bytes;
     s->n_syms = in->n_syms;
     s->freq = in->freq;
+    s->n_tables = in->n_tables;
+    s->tid = in->tid;
     s->words = in->words;
     s->pinned_words = in->pinned_words;
     std::memcpy(s->final_x, in->final_x, sizeof s->final_x);
@@ -367,6 +410,7 @@ int recoil_stream_info(const recoil_stream* s, recoil_info* o) {
   o->n_bits = s->n_bits;
   o->sym_bytes = s->sym_bytes;
   o->alphabet = s->alphabet();
+  o->n_tables = s->n_tables;
   o->bitstream_bytes = 2 * o->n_words + 4ull * kW;
   o->metadata_bytes = (uint64_t)s->entries.size() * (8 + 2 * kW + 4 * kW);
   for (const Entry& e : s->entries) {

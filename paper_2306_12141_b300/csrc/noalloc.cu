@@ -65,6 +65,8 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
                                      void* cuda_stream) {
   clear_error();
   if (!s || (!d_out && s->n_syms)) return fail(RECOIL_EINVAL, "null argument");
+  if (s->adaptive())
+    return fail(RECOIL_EINVAL, "adaptive streams keep their table numbers in a workspace: use the plan API");
   const size_t need_words = (s->n_words() + kChunkWords - 1) / kChunkWords * kChunkWords * 2;
   if (need_words && (!d_words || words_bytes < need_words))
     return fail(RECOIL_EINVAL, "d_words must hold the stream's words padded to a multiple of 256 words (" +
@@ -123,8 +125,9 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
     a.kind = k;
     a.persistent = 1;
     a.table_smem = (uint32_t)((img.kind_smem[k] + 15) / 16 * 16);
+    a.depth = img.kind_depth[k];
     int per_sm = 0;
-    if (occupancy_ctas_per_sm(k, img.warps, a.table_smem, &per_sm) != 0 || per_sm <= 0) {
+    if (occupancy_ctas_per_sm(k, img.warps, a.depth, a.table_smem, &per_sm) != 0 || per_sm <= 0) {
       recoil_plan_free(plan);
       return fail(RECOIL_ECUDA, "occupancy query failed");
     }

@@ -177,11 +177,7 @@ int recoil_pipeline_run(recoil_pipeline* P, void* const* h_outs, void* d_ws, siz
     if (e == cudaSuccess && G.table_bytes)
       e = cudaMemcpyAsync(gws + G.off_tables, G.tables, G.table_bytes, cudaMemcpyHostToDevice, P->s_in);
     const std::vector<const Stream*>& ss = plan_streams(G.plan);
-    const std::vector<uint64_t>& wo = plan_word_offsets(G.plan);
-    for (size_t k = 0; k < ss.size() && e == cudaSuccess; k++) {
-      if (!ss[k]->n_words()) continue;
-      e = cudaMemcpyAsync(gws + wo[k] * 2, ss[k]->word_data(), ss[k]->n_words() * 2, cudaMemcpyHostToDevice, P->s_in);
-    }
+    for (size_t k = 0; k < ss.size() && e == cudaSuccess; k++) e = plan_upload_stream(G.plan, k, gws, P->s_in);
     if (e == cudaSuccess) e = cudaEventRecord(G.in, P->s_in);
     if (e != cudaSuccess) break;
     // decode, once the copy-in is there and the previous copy-out left the staging

@@ -22,9 +22,25 @@ constexpr uint32_t kMaxSmem = 227 * 1024;
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 uint32_t table_kind_of(const Stream& s) {
+  if (s.adaptive()) return s.sym_bytes == 2 ? kAdaptive16 : kAdaptive8;
   if (s.sym_bytes == 2) return kGeneric16;
   if (s.n_bits <= 12 && !s.constant()) return kPacked8;
   return kGeneric8;
+}
+
+// 16-bit entries between the CDF rows of an adaptive model: at least A + 1,
+// an odd number of 32-bit words so that the same position in different rows
+// falls in different shared-memory banks.
+uint32_t adaptive_row_stride(uint32_t A) {
+  uint32_t words = (A + 2) / 2;
+  if (!(words & 1)) words++;
+  return 2 * words;
+}
+
+uint32_t adaptive_depth(uint32_t A) {
+  uint32_t d = 0;
+  while ((1u << d) < A) d++;
+  return d;
 }
 
 // Decoder tables of a stream (built once and cached on the stream).
@@ -34,7 +50,19 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
   const uint32_t k = table_kind_of(s);
   const uint32_t sb = (uint32_t)align_up((size_t)slots * 2, 16);
   if (s.table_img.empty()) {
-    if (k == kPacked8) {
+    if (k == kAdaptive8 || k == kAdaptive16) {
+      // one row per PDF: F(0..A) as 16-bit values, F(A) = 2^n kept modulo 2^16
+      const uint32_t stride = adaptive_row_stride(A);
+      s.table_img.assign(align_up((size_t)s.n_tables * stride * 2, 16), 0);
+      uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data());
+      for (uint32_t t = 0; t < s.n_tables; t++) {
+        uint32_t F = 0;
+        for (uint32_t sym = 0; sym <= A; sym++) {
+          cdf[(size_t)t * stride + sym] = (uint16_t)F;
+          if (sym < A) F += s.freq[(size_t)t * A + sym];
+        }
+      }
+    } else if (k == kPacked8) {
       s.table_img.assign(align_up((size_t)slots * 4, 16), 0);
       uint32_t* lut = reinterpret_cast<uint32_t*>(s.table_img.data());
       uint32_t F = 0;
@@ -58,7 +86,7 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
     s.table_kind = k;
   }
   *kind = s.table_kind;
-  *slot_bytes = k == kPacked8 ? 0 : sb;
+  *slot_bytes = (k == kGeneric8 || k == kGeneric16) ? sb : 0;
   return s.table_img;
 }
 
@@ -122,8 +150,9 @@ struct recoil_plan {
   size_t off_outs = 0, off_streams = 0, off_items = 0, off_entries = 0;
   size_t off_tables = 0, off_meta = 0, ws_bytes = 0;   // words start at 0
   std::vector<uint64_t> word_off;                      // per stream, in words
+  std::vector<uint64_t> tid_off;                       // per adaptive stream: its table numbers, in words
   uint32_t n_items = 0;
-  uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {};
+  uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {}, kind_depth[kKinds] = {};
   std::vector<uint32_t> stream_kind, stream_item_first, stream_item_count;
 
   uint8_t* d_ws = nullptr;
@@ -157,6 +186,7 @@ static int plan_build(recoil_plan* P) {
   size_t table_off = 0;
   uint64_t word_off = 0;
   P->word_off.resize(count);
+  P->tid_off.assign(count, 0);
   P->stream_kind.resize(count);
   std::vector<std::pair<size_t, const std::vector<uint8_t>*>> tabs;
   for (uint32_t i = 0; i < count; i++) {
@@ -179,7 +209,20 @@ static int plan_build(recoil_plan* P) {
     tabs.push_back({table_off, &img});
     table_off += img.size();
     word_off += align_up(s.n_words(), kChunkWords);
+    if (s.adaptive()) {
+      // the table numbers follow the words, one byte per symbol, on a chunk boundary
+      d.tid = word_off;
+      d.row_stride = adaptive_row_stride(s.alphabet());
+      d.depth = adaptive_depth(s.alphabet());
+      d.n_tables = s.n_tables;
+      P->tid_off[i] = word_off;
+      word_off += align_up((s.n_syms + 1) / 2, kChunkWords);
+    }
     P->kind_smem[kind] = std::max<uint32_t>(P->kind_smem[kind], d.table_bytes);
+    if (s.adaptive()) {
+      if (!adaptive_warps_supported(warps)) return fail(RECOIL_EINVAL, "adaptive streams decode with 4, 8 or 16 warps per CTA");
+      P->kind_depth[kind] = std::max(P->kind_depth[kind], adaptive_depth_class(s.alphabet()));
+    }
 
     const size_t first = entries.size();
     build_entries(s, i, entries);
@@ -187,7 +230,7 @@ static int plan_build(recoil_plan* P) {
     // previous stream's last work item (one staged table serves both)
     const bool same_table = i > 0 && !per_stream && !items.empty() && items.back().kind == kind &&
                             P->streams[i - 1]->n_bits == s.n_bits && P->streams[i - 1]->sym_bytes == s.sym_bytes &&
-                            P->streams[i - 1]->freq == s.freq &&
+                            P->streams[i - 1]->n_tables == s.n_tables && P->streams[i - 1]->freq == s.freq &&
                             items.back().it.entry + items.back().it.count == first;
     size_t e = first;
     if (same_table && items.back().it.count < warps) {
@@ -265,6 +308,7 @@ void plan_image(const recoil_plan* P, PlanImage* o) {
     o->kind_first[k] = P->kind_first[k];
     o->kind_count[k] = P->kind_count[k];
     o->kind_smem[k] = P->kind_smem[k];
+    o->kind_depth[k] = P->kind_depth[k];
   }
 }
 }  // namespace recoil
@@ -274,9 +318,18 @@ static int cuda_fail(cudaError_t e, const char* what) {
 }
 
 namespace recoil {
+cudaError_t plan_upload_stream(const recoil_plan* P, size_t i, uint8_t* ws, cudaStream_t cs) {
+  const Stream& s = *P->streams[i];
+  cudaError_t e = cudaSuccess;
+  if (s.n_words())
+    e = cudaMemcpyAsync(ws + P->word_off[i] * 2, s.word_data(), s.n_words() * 2, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && s.adaptive() && s.n_syms)
+    e = cudaMemcpyAsync(ws + P->tid_off[i] * 2, s.tid->data(), s.n_syms, cudaMemcpyHostToDevice, cs);
+  return e;
+}
+
 size_t plan_bulk_bytes(const recoil_plan* P) { return P->off_meta; }
 const std::vector<const Stream*>& plan_streams(const recoil_plan* P) { return P->streams; }
-const std::vector<uint64_t>& plan_word_offsets(const recoil_plan* P) { return P->word_off; }
 
 int plan_upload_parts(recoil_plan* P, void* d_ws, size_t ws_bytes, cudaStream_t cs, bool bulk, bool meta) {
   if (!P || !d_ws) return fail(RECOIL_EINVAL, "null argument");
@@ -294,11 +347,7 @@ int plan_upload_parts(recoil_plan* P, void* d_ws, size_t ws_bytes, cudaStream_t 
   if (bulk) {
     if (e == cudaSuccess && !P->tables.empty())
       e = cudaMemcpyAsync(ws + P->off_tables, P->tables.data(), P->tables.size(), cudaMemcpyHostToDevice, cs);
-    for (size_t i = 0; e == cudaSuccess && i < P->streams.size(); i++) {
-      const Stream& s = *P->streams[i];
-      if (!s.n_words()) continue;
-      e = cudaMemcpyAsync(ws + P->word_off[i] * 2, s.word_data(), s.n_words() * 2, cudaMemcpyHostToDevice, cs);
-    }
+    for (size_t i = 0; e == cudaSuccess && i < P->streams.size(); i++) e = plan_upload_stream(P, i, ws, cs);
   }
   if (e != cudaSuccess) return cuda_fail(e, "upload");
   if (P->d_ws != ws && P->graph) {
@@ -336,6 +385,7 @@ static int plan_launch(recoil_plan* P, cudaStream_t cs) {
       a.kind = k;
       a.persistent = 0;
       a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
+      a.depth = P->kind_depth[k];
       e = launch_decode(k, a, a.n_items, cs);
       if (e != cudaSuccess) return cuda_fail(e, "decode launch");
       P->launches++;
@@ -349,8 +399,9 @@ static int plan_launch(recoil_plan* P, cudaStream_t cs) {
     a.kind = k;
     a.persistent = 1;
     a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
+    a.depth = P->kind_depth[k];
     int per_sm = (int)P->opts.ctas_per_sm;
-    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, a.table_smem, &per_sm) != 0)
+    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, a.depth, a.table_smem, &per_sm) != 0)
       return fail(RECOIL_ECUDA, "occupancy query failed");
     if (per_sm <= 0) return fail(RECOIL_EINVAL, "kernel does not fit on an SM with these options");
     const unsigned grid = (unsigned)std::min<uint64_t>(a.n_items, (uint64_t)per_sm * P->sms);

@@ -28,8 +28,15 @@ enum TableKind : uint32_t {
   kPacked8 = 0,    // 8-bit symbols, n <= 12, f < 4096: one u32 per slot = bias | sym << 12 | f << 20
   kGeneric8 = 1,   // 8-bit symbols otherwise: u16 slot -> symbol, u32 symbol -> (f-1) << 16 | F
   kGeneric16 = 2,  // 16-bit symbols: same tables as kGeneric8, 16-bit stores
-  kKinds = 3,
+  kAdaptive8 = 3,  // adaptive model (a PDF row per symbol index), 8-bit symbols: u16 CDF rows
+  kAdaptive16 = 4, // adaptive model, 16-bit symbols
+  kKinds = 5,
 };
+
+// Longest alphabet of an adaptive model (the decoder's CDF search covers 2^12 symbols).
+constexpr uint32_t kMaxAdaptiveAlphabet = 4096;
+// Most PDF rows of an adaptive model (a table number is one byte per symbol).
+constexpr uint32_t kMaxTables = 256;
 
 // One split entry as kept on the host (Sec. 4.1 metadata, unpacked).
 struct Entry {
@@ -44,7 +51,9 @@ struct Stream {
   uint32_t n_bits = 0;
   uint32_t sym_bytes = 1;
   uint64_t n_syms = 0;
-  std::vector<uint32_t> freq;                      // quantised PDF f over the alphabet
+  std::vector<uint32_t> freq;                      // quantised PDF f over the alphabet (adaptive: n_tables rows)
+  uint32_t n_tables = 0;                           // adaptive model: PDF rows (0: one static PDF)
+  std::shared_ptr<const std::vector<uint8_t>> tid; // adaptive model: PDF row of every symbol index (Sec. 3.1)
   std::shared_ptr<const std::vector<uint16_t>> words;
   std::shared_ptr<const uint16_t> pinned_words;    // optional page-locked copy, shared with combined streams
   uint32_t final_x[kW] = {};
@@ -57,8 +66,9 @@ struct Stream {
 
   uint64_t n_words() const { return words ? words->size() : 0; }
   const uint16_t* word_data() const { return pinned_words ? pinned_words.get() : (words ? words->data() : nullptr); }
-  uint32_t alphabet() const { return (uint32_t)freq.size(); }
-  bool constant() const;                           // a single symbol owns all 2^n slots
+  uint32_t alphabet() const { return (uint32_t)(n_tables ? freq.size() / n_tables : freq.size()); }
+  bool adaptive() const { return n_tables != 0; }
+  bool constant() const;                           // a single symbol owns all 2^n slots (static model)
 };
 
 // ------------------------------------------------------------ device images
@@ -79,16 +89,19 @@ static_assert(sizeof(DevEntry) == 32 + 8 * kW, "DevEntry layout");
 struct alignas(16) DevStream {
   uint64_t words;            // element offset of the stream's words in the word pool (multiple of 256)
   uint64_t table;            // byte offset of the stream's tables in the table pool (multiple of 16)
+  uint64_t tid;              // adaptive: element offset (16-bit units) of its table-number bytes in the word pool
   uint32_t n_words;
   uint32_t n_bits;
   uint32_t kind;             // TableKind
   uint32_t alphabet;
   uint32_t sym_bytes;
   uint32_t table_bytes;      // bytes of the table image (multiple of 16)
-  uint32_t slot_bytes;       // generic kind: bytes of the slot -> symbol part (multiple of 16)
-  uint32_t pad;
+  uint32_t slot_bytes;       // generic kinds: bytes of the slot -> symbol part (multiple of 16)
+  uint32_t row_stride;       // adaptive: 16-bit entries between CDF rows (odd number of 32-bit words)
+  uint32_t depth;            // adaptive: steps of the CDF search, ceil(log2(alphabet))
+  uint32_t n_tables;         // adaptive: CDF rows
 };
-static_assert(sizeof(DevStream) == 48, "DevStream layout");
+static_assert(sizeof(DevStream) == 64, "DevStream layout");
 
 // A unit of work for one CTA: up to warps_per_cta consecutive entries, of one
 // stream or of consecutive streams whose decoder tables are identical.
@@ -100,12 +113,13 @@ struct alignas(16) DevItem {
 };
 
 struct alignas(16) DevControl {
-  uint32_t head[4];          // persistent queue position, one per table kind
+  uint32_t head[8];          // persistent queue position, one per table kind
   uint32_t errors;           // kErr* bits
   uint32_t bad_entry;        // an entry that raised an error (+1), 0 if none
-  uint32_t pad[58];
+  uint32_t pad[54];
 };
 static_assert(sizeof(DevControl) == 256, "DevControl layout");
+static_assert(kKinds <= 8, "one queue head per table kind");
 
 // Error flags raised by kernels.
 constexpr uint32_t kErrCorrupt = 1u;         // a state differs from the previous entry's record, or the
@@ -126,13 +140,16 @@ struct LaunchArgs {
   DevControl* control;
   uint32_t table_smem;       // bytes reserved for tables in shared memory
   uint32_t warps;            // warps per CTA
+  uint32_t depth;            // adaptive kinds: CDF search steps of the launch (4, 8 or 12)
 };
 
 // Kernel launchers (decode_kernels.cu).
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s);
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out);
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t depth, uint32_t table_smem, int* out);
 size_t ring_smem_per_warp();
 bool warps_supported(uint32_t warps);   // CTA sizes the kernels are built for: 1, 2, 4, 8, 16, 32 warps
+bool adaptive_warps_supported(uint32_t warps);   // adaptive kinds: 4, 8, 16 warps
+uint32_t adaptive_depth_class(uint32_t alphabet); // CDF search steps built for an alphabet (0: too large)
 
 // Host images of a plan (plan.cpp), for entry points that place them in
 // device memory of their own. meta = control, output pointers, stream
@@ -145,7 +162,7 @@ struct PlanImage {
   size_t table_bytes;
   size_t ws_off_tables;      // workspace offset of the tables (words start at 0)
   uint32_t warps;
-  uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds];
+  uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds], kind_depth[kKinds];
 };
 }  // namespace recoil
 struct recoil_plan;
@@ -157,9 +174,10 @@ void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>
 int plan_upload_parts(recoil_plan* plan, void* d_ws, size_t ws_bytes, cudaStream_t s, bool bulk, bool meta);
 // Bytes of the bulk region at the start of a plan's workspace.
 size_t plan_bulk_bytes(const recoil_plan* plan);
-// The streams a plan decodes (after combining) and their word offsets (in words).
+// The streams a plan decodes (after combining).
 const std::vector<const Stream*>& plan_streams(const recoil_plan* plan);
-const std::vector<uint64_t>& plan_word_offsets(const recoil_plan* plan);
+// Copy stream k's bulk data (words; table numbers of an adaptive stream) to its place in ws.
+cudaError_t plan_upload_stream(const recoil_plan* plan, size_t k, uint8_t* ws, cudaStream_t s);
 
 // Error reporting (thread-local message).
 int fail(int code, const std::string& msg);

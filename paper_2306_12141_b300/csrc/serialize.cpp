@@ -119,6 +119,7 @@ bool get_signed(BitReader& br, size_t count, std::vector<int64_t>& v) {
 uint64_t ceil_div(uint64_t a, uint64_t b) { return b ? (a + b - 1) / b : 0; }
 
 int pack_metadata(const Stream& s, std::vector<uint8_t>& out) {
+  if (s.adaptive()) return fail(RECOIL_EINVAL, "adaptive streams are not serialised (their model travels with the codec)");
   const uint64_t M = s.entries.size() + 1, B = s.n_words(), N = s.n_syms;
   const uint64_t Eb = ceil_div(B, M), Eg = ceil_div(ceil_div(N, kW), M);
   BitWriter bw(out);

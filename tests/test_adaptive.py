@@ -1,0 +1,195 @@
+"""Adaptive coding (Sec. 3.1: the PDF of every coding step is chosen by the
+symbol index) in the library, against the oracle.
+
+CPU: the library's adaptive encoder gives the oracle's words, final states and
+split entries bit for bit, and rejects malformed models. GPU: the adaptive
+decode kernels reproduce the input and the oracle's split decode, alone, in
+batches mixed with static streams, at every combine count and CTA size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+
+def _case(N, seed, n_bits=16, sym_bytes=2, n_tables=64, alphabet=256):
+    a = workloads.AdaptiveStream("t", N, n_bits=n_bits, sym_bytes=sym_bytes, n_tables=n_tables,
+                                 alphabet=alphabet, seed=seed)
+    tables = a.tables()
+    s, tid = a.draw()
+    return a, tables, s, tid
+
+
+def _same(R, s, tid, tables, n, M):
+    p = R.encode_adaptive(s, n, tables, tid, M)
+    o = oracle.encode_adaptive_with_splits(s, tid, tables, n, M)
+    e = p.export()
+    assert np.array_equal(e["freq"].reshape(tables.shape), tables)
+    assert np.array_equal(e["words"], o.words)
+    assert np.array_equal(e["final"], o.final)
+    assert np.array_equal(e["entry_word"].astype(np.int64), o.q)
+    assert np.array_equal(e["entry_index"].astype(np.int64), o.idx[:-1])
+    assert np.array_equal(e["entry_state"].astype(np.uint32), o.y[:-1])
+    return p, o
+
+
+CASES = [
+    dict(n_bits=16, sym_bytes=2, n_tables=64, alphabet=256),
+    dict(n_bits=12, sym_bytes=1, n_tables=16, alphabet=256),
+    dict(n_bits=11, sym_bytes=2, n_tables=3, alphabet=1000),
+    dict(n_bits=14, sym_bytes=2, n_tables=8, alphabet=4096),
+    dict(n_bits=8, sym_bytes=1, n_tables=256, alphabet=12),
+]
+
+
+@pytest.mark.parametrize("cfg", CASES, ids=lambda c: f"n{c['n_bits']}_A{c['alphabet']}_T{c['n_tables']}")
+@pytest.mark.parametrize("M", [1, 7, 200])
+def test_adaptive_encoder_matches_oracle(recoil_lib, cfg, M):
+    a, tables, s, tid = _case(100_003, 5, **cfg)
+    p, _ = _same(recoil_lib, s, tid, tables, cfg["n_bits"], M)
+    info = p.info
+    assert info["n_tables"] == cfg["n_tables"] and info["alphabet"] == cfg["alphabet"]
+
+
+@pytest.mark.parametrize("N", [0, 1, 31, 32, 33, 65, 1023])
+def test_adaptive_edge_lengths(recoil_lib, N):
+    a, tables, s, tid = _case(max(N, 1), N + 100)
+    s, tid = s[:N], tid[:N]
+    if N == 0:
+        p = recoil_lib.encode_adaptive(s, 16, tables, tid, 4)
+        assert p.info["n_words"] == 0 and p.info["n_entries"] == 1
+        return
+    _same(recoil_lib, s, tid, tables, 16, 4)
+
+
+def test_combine_keeps_the_model(recoil_lib):
+    R = recoil_lib
+    a, tables, s, tid = _case(50_000, 9)
+    p = R.encode_adaptive(s, 16, tables, tid, 40)
+    c = R.combine_splits(p, 5)
+    assert c.info["n_tables"] == 64 and c.info["n_entries"] == 5
+    assert np.array_equal(R.stream_freq(c), tables)
+    with pytest.raises(R.RecoilError):
+        R.serialize(c)                            # the model travels with the codec
+
+
+def test_adaptive_rejects_bad_models(recoil_lib):
+    R = recoil_lib
+    a, tables, s, tid = _case(2000, 10)
+    bad = tables.copy()
+    bad[3, 7] += 1                                # row 3 sums to 2^n + 1
+    zero = tables.copy()
+    zero[5, 0] += zero[5, 1] - 0
+    zero[5, 1] = 0                                # a zero frequency (sum unchanged)
+    big_tid = tid.copy()
+    big_tid[17] = 64                              # table number out of range
+    big_sym = s.copy()
+    big_sym[3] = 256                              # symbol outside the alphabet
+    for args in ((s, 16, bad, tid), (s, 16, zero, tid), (s, 16, tables, big_tid), (big_sym, 16, tables, tid),
+                 (s, 7, tables, tid)):            # alphabet 256 > 2^7
+        with pytest.raises(R.RecoilError) as e:
+            R.encode_adaptive(*args, 8)
+        assert e.value.code == R.EINVAL
+    with pytest.raises(R.RecoilError):
+        R.encode_adaptive(s, 16, tables[:1].repeat(257, axis=0), np.zeros_like(tid), 8)   # 257 tables
+
+
+def test_adaptive_rejected_by_noalloc_and_small_ctas(recoil_lib):
+    R = recoil_lib
+    a, tables, s, tid = _case(4000, 11)
+    p = R.encode_adaptive(s, 16, tables, tid, 4)
+    for w in (1, 2, 32):
+        with pytest.raises(R.RecoilError):
+            R.Plan([p], {"warps_per_cta": w})
+
+
+# ------------------------------------------------------------------- GPU
+def _gpu_decode(R, streams, opts=None):
+    import torch
+    plan = R.Plan(streams, opts)
+    ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device="cuda")
+    infos = [s.info for s in streams]
+    outs = [torch.full((max(1, i["n_syms"] * i["sym_bytes"]),), 0xAB, dtype=torch.uint8, device="cuda")
+            for i in infos]
+    plan.upload(ws)
+    plan.decode([o.data_ptr() for o in outs])
+    assert plan.errors() == 0, R.recoil_last_error()
+    res = []
+    for o, i in zip(outs, infos):
+        x = o.cpu().numpy()[: i["n_syms"] * i["sym_bytes"]]
+        res.append(x.view(np.uint16) if i["sym_bytes"] == 2 else x)
+    return res
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cfg", CASES, ids=lambda c: f"n{c['n_bits']}_A{c['alphabet']}_T{c['n_tables']}")
+def test_gpu_adaptive_matches_oracle(recoil_lib, cfg):
+    R = recoil_lib
+    a, tables, s, tid = _case(400_009, 21, **cfg)
+    p = R.encode_adaptive(s, cfg["n_bits"], tables, tid, 256)
+    o = oracle.encode_adaptive_with_splits(s, tid, tables, cfg["n_bits"], 256)
+    for Mp in (256, 37, 1):
+        (out,) = _gpu_decode(R, [R.combine_splits(p, Mp)])
+        assert np.array_equal(out, s), Mp
+        assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(out.dtype)), Mp
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("warps", [4, 8, 16])
+def test_gpu_adaptive_cta_sizes_and_graph(recoil_lib, warps):
+    R = recoil_lib
+    a, tables, s, tid = _case(1_000_003, 22)
+    p = R.encode_adaptive(s, 16, tables, tid, 1024)
+    for opts in ({"warps_per_cta": warps}, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH},
+                 {"warps_per_cta": warps, "flags": R.BATCH_PER_STREAM}, {"warps_per_cta": warps,
+                                                                         "split_symbols": 20000}):
+        (out,) = _gpu_decode(R, [p], opts)
+        assert np.array_equal(out, s), opts
+
+
+@pytest.mark.gpu
+def test_gpu_adaptive_mixed_batch(recoil_lib):
+    """Adaptive streams of both symbol sizes next to static streams of every kind, one plan."""
+    R = recoil_lib
+    streams, want = [], []
+    for k, cfg in enumerate(CASES):
+        a, tables, s, tid = _case(50_000 + 7919 * k, 30 + k, **cfg)
+        streams.append(R.encode_adaptive(s, cfg["n_bits"], tables, tid, 20))
+        want.append(s)
+    for k, st in enumerate([workloads.Stream("z", 70_001, 1, 12, "zipf", {"s": 1.2}, seed=40),
+                            workloads.Stream("g", 30_011, 2, 15, "gauss16",
+                                             {"mean": 2048.0, "sigma": 200.0, "k": 4096}, seed=41),
+                            workloads.Stream("e", 20_000, 1, 16, "expbytes", {"lam": 100.0}, seed=42)]):
+        s = st.symbols()
+        streams.append(R.encode_with_splits(s, st.n_bits, 9))
+        want.append(s)
+    order = np.random.default_rng(3).permutation(len(streams))
+    outs = _gpu_decode(R, [streams[i] for i in order], {"warps_per_cta": 8})
+    for out, i in zip(outs, order):
+        assert np.array_equal(out, want[i]), i
+
+
+@pytest.mark.gpu
+def test_gpu_adaptive_full_size_sampled(recoil_lib):
+    """The 256 MiB adaptive workload in the launch shape the benchmark times: the whole
+    output against the input, and a sample of split threads against the oracle's."""
+    R = recoil_lib
+    a = workloads.adaptive_256mib()
+    tables = a.tables()
+    s, tid = a.draw()
+    p = R.encode_adaptive(s, a.n_bits, tables, tid, 65536)
+    c = R.combine_splits(p, 9472)
+    (out,) = _gpu_decode(R, [c], {"warps_per_cta": 8})
+    assert np.array_equal(out, s)
+    # sampled threads of the oracle on the same entries
+    e = c.export()
+    K = c.info["n_entries"]
+    idx = np.vstack([e["entry_index"].astype(np.int64), np.zeros((1, 32), dtype=np.int64)])
+    y = np.vstack([e["entry_state"].astype(np.uint32), e["final"][None, :]])
+    st = oracle.OracleStream(len(s), a.n_bits, 32, 16, 16, tables, e["words"], e["final"], None, None,
+                             e["entry_word"].astype(np.int64), idx, y, tid)
+    for k in np.random.default_rng(5).choice(K, size=6, replace=False):
+        lo, hi = oracle.owned_range(st, int(k))
+        ref = oracle.decode_thread(st, int(k))
+        assert np.array_equal(out[lo:hi + 1], ref[lo:hi + 1].astype(np.uint16)), k
