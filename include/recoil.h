@@ -264,6 +264,25 @@ void recoil_plan_free(recoil_plan* plan);
  */
 int recoil_shard(const recoil_stream* const* streams, uint32_t count, uint32_t world, uint32_t* rank_of);
 
+/*
+ * One stream over `world` ranks (one GPU each): the stream's kept entries are
+ * cut into `world` contiguous runs of about equal owned symbols, and rank
+ * `rank` gets a plan that decodes only its run. Each run owns a contiguous
+ * symbol range [*sym_lo, *sym_hi) (Sec. 4.1.3 ownership), the ranges of all
+ * ranks tile [0, N), and the runs share nothing, so the ranks decode with no
+ * exchange; the result is the concatenation of the ranges. Combine first
+ * (recoil_combine_splits) to choose the split count. opts as for
+ * recoil_plan_create (its split_symbols must be 0). The plan's decode takes
+ * one output pointer to a buffer of (*sym_hi - *sym_lo) * sym_bytes bytes
+ * that receives symbols *sym_lo ..; the workspace holds the whole stream's
+ * words. A rank whose run is empty gets sym_lo == sym_hi and a plan that
+ * launches nothing. Errors: EINVAL (null, world < 1, rank >= world,
+ * split_symbols set), ENOMEM.
+ */
+int recoil_plan_create_shard(const recoil_stream* stream, uint32_t world, uint32_t rank,
+                             const recoil_batch_opts* opts, recoil_plan** out, uint64_t* sym_lo,
+                             uint64_t* sym_hi);
+
 /* Workspace bytes recoil_decode_batch needs for these streams and options. */
 int recoil_workspace_size(const recoil_stream* const* streams, uint32_t count,
                           const recoil_batch_opts* opts, size_t* bytes);

@@ -80,6 +80,7 @@ EXPORTS = [
     "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
     "recoil_pipeline_free", "recoil_shard", "recoil_encode_with_table",
     "recoil_serialized_size", "recoil_serialize", "recoil_deserialize", "recoil_encode_adaptive",
+    "recoil_plan_create_shard",
 ]
 
 _lib = None
@@ -122,6 +123,7 @@ def lib():
         L.recoil_decode_batch.argtypes = [vp, u32, vp, vp, C.c_size_t, vp, C.POINTER(BatchOpts)]
         L.recoil_decode_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
         L.recoil_shard.argtypes = [vp, u32, u32, vp]
+        L.recoil_plan_create_shard.argtypes = [vp, u32, u32, C.POINTER(BatchOpts), pp, C.POINTER(u64), C.POINTER(u64)]
         L.recoil_pipeline_create.argtypes = [vp, u32, C.POINTER(BatchOpts), u32, pp]
         L.recoil_pipeline_sizes.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         L.recoil_pipeline_run.argtypes = [vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp]
@@ -329,13 +331,26 @@ def _ptr_array(ptrs) -> C.Array:
 class Plan:
     """A recoil_plan: device image layout and work queue of a batch of streams."""
 
-    def __init__(self, streams, opts=None):
+    def __init__(self, streams, opts=None, _handle=None):
         self.streams = list(streams)          # keep the host streams alive
+        if _handle is not None:
+            self.handle = _handle
+            return
         h = C.c_void_p()
         o = _opts(opts)
         _check(lib().recoil_plan_create(_handles(self.streams), len(self.streams),
                                         C.byref(o) if o is not None else None, C.byref(h)))
         self.handle = h.value
+
+    @classmethod
+    def shard(cls, stream, world: int, rank: int, opts=None):
+        """recoil_plan_create_shard: (plan, sym_lo, sym_hi) of rank's contiguous run of splits."""
+        h = C.c_void_p()
+        o = _opts(opts)
+        lo, hi = C.c_uint64(), C.c_uint64()
+        _check(lib().recoil_plan_create_shard(stream.handle, world, rank, C.byref(o) if o is not None else None,
+                                              C.byref(h), C.byref(lo), C.byref(hi)))
+        return cls([stream], _handle=h.value), lo.value, hi.value
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -370,6 +385,11 @@ class Plan:
 
 def recoil_plan_create(streams, opts=None) -> Plan:
     return Plan(streams, opts)
+
+
+def recoil_plan_create_shard(stream, world: int, rank: int, opts=None):
+    """(plan, sym_lo, sym_hi): rank's contiguous run of the stream's splits (see recoil.h)."""
+    return Plan.shard(stream, world, rank, opts)
 
 
 def recoil_workspace_size(streams, opts=None) -> int:

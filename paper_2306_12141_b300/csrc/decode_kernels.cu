@@ -81,52 +81,70 @@ struct Tables {
 };
 
 // Adaptive model (Sec. 3.1): symbol i is coded with PDF row tid[i]. Row t
-// holds F(0..A) of PDF t as 16-bit values (F(A) = 2^n modulo 2^16). The
-// symbol is the last s with F(s) <= slot, found by DEPTH halvings
-// (2^DEPTH >= A, probes at or beyond A skipped); f = F(s+1) - F(s) modulo
-// 2^16, exact since every f of an adaptive model is below 2^16.
-template <uint32_t KIND, int DEPTH>
+// holds H(s) = F(s) - 1 modulo 2^16 of PDF t for s = 0..A (H(0) = 0xffff,
+// H(A) = 2^n - 1): the symbol is the last s with F(s) <= slot, i.e. with
+// H(s) < slot for s >= 1; then F(s) = H(s) + 1 and f = H(s+1) - H(s), both
+// modulo 2^16 and exact since every f of an adaptive model is below 2^16.
+//
+// GUIDED (alphabets up to 256): the row's guide holds, for each of 2^g equal
+// buckets of slots, the symbol owning the bucket's first slot; the symbol of
+// `slot` lies between the guides of its bucket and of the next, and a binary
+// search narrows that range (usually empty: one lookup). Otherwise a 12-step
+// binary search over the whole row.
+template <bool GUIDED>
 struct AdaptiveTables {
   const uint16_t* cdf;
-  uint32_t stride, A;
+  const uint8_t* guide;
+  uint32_t stride, gstride, gshift, A;
   __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream& st) {
     cdf = reinterpret_cast<const uint16_t*>(smem);
+    guide = smem + (size_t)st.n_tables * st.row_stride * 2;
     stride = st.row_stride;
+    gstride = st.guide_stride;
+    gshift = st.n_bits > kGuideBits ? st.n_bits - kGuideBits : 0;
     A = st.alphabet;
   }
   __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask, uint32_t t) const {
     const uint32_t slot = x & mask;
     const uint16_t* row = cdf + t * stride;
-    uint32_t s = 0;
+    uint32_t s;
+    if (GUIDED) {
+      const uint8_t* gd = guide + t * gstride;
+      const uint32_t b = slot >> gshift;
+      s = gd[b];
+      uint32_t hi = gd[b + 1];
+      while (s < hi) {                                  // bounded: hi - s halves
+        const uint32_t mid = (s + hi + 1) >> 1;
+        if (row[mid] < slot) s = mid; else hi = mid - 1;
+      }
+    } else {
+      s = 0;
 #pragma unroll
-    for (int k = DEPTH - 1; k >= 0; --k) {
-      const uint32_t m = s | (1u << k);
-      if (m < A && row[m] <= slot) s = m;
+      for (int k = 11; k >= 0; --k) {
+        const uint32_t m = s | (1u << k);
+        if (m < A && row[m] < slot) s = m;
+      }
     }
-    const uint32_t F0 = row[s];
-    const uint32_t f = (uint32_t)(uint16_t)(row[s + 1] - F0);
-    x = f * (x >> n) + slot - F0;
+    const uint32_t h0 = row[s];
+    const uint32_t f = (row[s + 1] - h0) & 0xffffu;
+    x = f * (x >> n) + slot - ((h0 + 1u) & 0xffffu);
     return s;
   }
 };
 
 template <uint32_t KIND>
 __host__ __device__ constexpr bool is_adaptive() {
-  return KIND == kAdaptive8 || KIND == kAdaptive16;
+  return is_adaptive_kind(KIND);
 }
 
-// Decoder tables of a kind (DEPTH only matters to adaptive kinds).
-template <uint32_t KIND, int DEPTH>
+// Decoder tables of a kind.
+template <uint32_t KIND, bool ADAPTIVE = is_adaptive_kind(KIND)>
 struct TablesOf {
   using T = Tables<KIND>;
 };
-template <int DEPTH>
-struct TablesOf<kAdaptive8, DEPTH> {
-  using T = AdaptiveTables<kAdaptive8, DEPTH>;
-};
-template <int DEPTH>
-struct TablesOf<kAdaptive16, DEPTH> {
-  using T = AdaptiveTables<kAdaptive16, DEPTH>;
+template <uint32_t KIND>
+struct TablesOf<KIND, true> {
+  using T = AdaptiveTables<adaptive_kind_guided(KIND)>;
 };
 
 template <uint32_t KIND>
@@ -141,6 +159,15 @@ template <>
 struct SymOut<kAdaptive16> {
   using T = uint16_t;
 };
+template <>
+struct SymOut<kAdaptive16Wide> {
+  using T = uint16_t;
+};
+
+// Bring the cache line of p into L1 (no register, no wait).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" : : "l"(p));
+}
 
 // A read-only load kept where it is written (volatile asm is neither merged
 // with an earlier load of the same address nor hoisted).
@@ -175,9 +202,9 @@ struct Walker {
   uint4 pre;           // prefetched chunk (cbase/256 - 2)
 };
 
-template <uint32_t KIND, int DEPTH>
+template <uint32_t KIND>
 struct EntryDecoder {
-  typename TablesOf<KIND, DEPTH>::T T;
+  typename TablesOf<KIND>::T T;
   const uint16_t* __restrict__ words;
   const uint8_t* __restrict__ tid;     // adaptive kinds: PDF row of every symbol index
   uint16_t* ring;
@@ -293,6 +320,9 @@ struct EntryDecoder {
       while (g - 7 >= steady_lo) {
         const int rp0 = w.rp;
         const int i0 = g * kW + lane;
+        // adaptive: table numbers of the block after next into L1 (256 bytes, 8 per lane)
+        if constexpr (is_adaptive<KIND>())
+          if (g >= 23) prefetch_l1(tid + (g - 23) * kW + lane * 8);
 #pragma unroll
         for (int u = 0; u < 8; ++u) sstep(w, o - u * kW, i0 - u * kW);
         o -= 8 * kW;
@@ -348,12 +378,53 @@ struct Residency {
   static constexpr int kMinBlocks = kWant < 1 ? 1 : (kWant > 32 ? 32 : kWant);
 };
 
-template <uint32_t KIND, int WARPS, int DEPTH>
+template <uint32_t KIND, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlocks)) decode_kernel(const LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item;
   const int warp = threadIdx.x >> 5;
   uint16_t* ring = reinterpret_cast<uint16_t*>(smem + a.table_smem) + warp * kRingSlots;
+
+  auto stage = [&](const DevStream& st) {
+    const uint4* src = reinterpret_cast<const uint4*>(a.table_pool + st.table);
+    uint4* dst = reinterpret_cast<uint4*>(smem);
+    const uint32_t n16 = st.table_bytes >> 4;
+    for (uint32_t k = threadIdx.x; k < n16; k += WARPS * 32) dst[k] = __ldg(src + k);
+  };
+  auto decode_entry = [&](const DevStream& st, uint32_t entry) {
+    // the entry's own stream: an item may span streams that share one table
+    const DevEntry* ent = a.entries + entry;
+    const uint32_t sid = ent->stream;
+    EntryDecoder<KIND> d;
+    d.T.bind(smem, st);
+    d.words = a.word_pool + a.streams[sid].words;
+    d.tid = reinterpret_cast<const uint8_t*>(a.word_pool + a.streams[sid].tid);
+    d.ring = ring;
+    d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[sid]);
+    d.n = st.n_bits;
+    d.mask = (1u << st.n_bits) - 1u;
+    d.gt = lanemask_gt();
+    d.lane = threadIdx.x & 31;
+    d.run(ent, a.control, entry);
+  };
+
+  if (a.warp_queue) {
+    // one table for the whole launch, one entry per item: stage once, then
+    // every warp pops items on its own (no barrier between entries)
+    const DevStream& st = a.streams[a.items[0].stream];
+    stage(st);
+    __syncthreads();
+    for (;;) {
+      uint32_t it = 0;
+      if ((threadIdx.x & 31) == 0) it = atomicAdd(&a.control->head[a.kind], 1u);
+      it = __shfl_sync(kFull, it, 0);
+      if (it >= a.n_items) break;
+      decode_entry(st, a.items[it].entry);
+    }
+    return;
+  }
+
+  // CTA items of up to WARPS entries; the table is restaged when the stream changes
   uint32_t staged = 0xffffffffu;
   uint32_t it = blockIdx.x;
   for (;;) {
@@ -366,29 +437,11 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlock
     const DevItem item = a.items[it];
     const DevStream& st = a.streams[item.stream];
     if (item.stream != staged) {
-      const uint4* src = reinterpret_cast<const uint4*>(a.table_pool + st.table);
-      uint4* dst = reinterpret_cast<uint4*>(smem);
-      const uint32_t n16 = st.table_bytes >> 4;
-      for (uint32_t k = threadIdx.x; k < n16; k += WARPS * 32) dst[k] = __ldg(src + k);
+      stage(st);
       staged = item.stream;
       __syncthreads();
     }
-    if ((uint32_t)warp < item.count) {
-      // the entry's own stream: an item may span streams that share one table
-      const DevEntry* ent = a.entries + item.entry + warp;
-      const uint32_t sid = ent->stream;
-      EntryDecoder<KIND, DEPTH> d;
-      d.T.bind(smem, st);
-      d.words = a.word_pool + a.streams[sid].words;
-      d.tid = reinterpret_cast<const uint8_t*>(a.word_pool + a.streams[sid].tid);
-      d.ring = ring;
-      d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[sid]);
-      d.n = st.n_bits;
-      d.mask = (1u << st.n_bits) - 1u;
-      d.gt = lanemask_gt();
-      d.lane = threadIdx.x & 31;
-      d.run(ent, a.control, item.entry + warp);
-    }
+    if ((uint32_t)warp < item.count) decode_entry(st, item.entry + warp);
     if (!a.persistent) break;
     __syncthreads();
   }
@@ -398,53 +451,24 @@ size_t smem_bytes(uint32_t warps, uint32_t table_smem) {
   return (size_t)table_smem + (size_t)warps * kRingSlots * sizeof(uint16_t);
 }
 
-template <uint32_t KIND, int WARPS, int DEPTH>
-cudaError_t launch_kwd(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+template <uint32_t KIND, int WARPS>
+cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   const size_t sm = smem_bytes(WARPS, a.table_smem);
-  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS, DEPTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  decode_kernel<KIND, WARPS, DEPTH><<<grid, WARPS * 32, sm, s>>>(a);
+  decode_kernel<KIND, WARPS><<<grid, WARPS * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-template <uint32_t KIND, int WARPS, int DEPTH>
-int occupancy_kwd(uint32_t table_smem, int* out) {
+template <uint32_t KIND, int WARPS>
+int occupancy_kw(uint32_t table_smem, int* out) {
   const size_t sm = smem_bytes(WARPS, table_smem);
-  if (cudaFuncSetAttribute(decode_kernel<KIND, WARPS, DEPTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+  if (cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return -1;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS, DEPTH>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
 }
 
-// Static kinds come in every CTA size; adaptive kinds in 4, 8 and 16 warps
-// and three search depths (alphabets up to 16, 256 and 4096 symbols).
-template <uint32_t KIND, int WARPS>
-cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  if constexpr (is_adaptive<KIND>()) {
-    switch (a.depth) {
-      case 4: return launch_kwd<KIND, WARPS, 4>(a, grid, s);
-      case 8: return launch_kwd<KIND, WARPS, 8>(a, grid, s);
-      case 12: return launch_kwd<KIND, WARPS, 12>(a, grid, s);
-    }
-    return cudaErrorInvalidValue;
-  } else {
-    return launch_kwd<KIND, WARPS, 0>(a, grid, s);
-  }
-}
-
-template <uint32_t KIND, int WARPS>
-int occupancy_kw(uint32_t depth, uint32_t table_smem, int* out) {
-  if constexpr (is_adaptive<KIND>()) {
-    switch (depth) {
-      case 4: return occupancy_kwd<KIND, WARPS, 4>(table_smem, out);
-      case 8: return occupancy_kwd<KIND, WARPS, 8>(table_smem, out);
-      case 12: return occupancy_kwd<KIND, WARPS, 12>(table_smem, out);
-    }
-    return -1;
-  } else {
-    return occupancy_kwd<KIND, WARPS, 0>(table_smem, out);
-  }
-}
-
+// Static kinds come in every CTA size, adaptive kinds in 4, 8 and 16 warps.
 template <uint32_t KIND>
 cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   if constexpr (is_adaptive<KIND>()) {
@@ -467,21 +491,21 @@ cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
 }
 
 template <uint32_t KIND>
-int occupancy_k(uint32_t warps, uint32_t depth, uint32_t table_smem, int* out) {
+int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
   if constexpr (is_adaptive<KIND>()) {
     switch (warps) {
-      case 4: return occupancy_kw<KIND, 4>(depth, table_smem, out);
-      case 8: return occupancy_kw<KIND, 8>(depth, table_smem, out);
-      case 16: return occupancy_kw<KIND, 16>(depth, table_smem, out);
+      case 4: return occupancy_kw<KIND, 4>(table_smem, out);
+      case 8: return occupancy_kw<KIND, 8>(table_smem, out);
+      case 16: return occupancy_kw<KIND, 16>(table_smem, out);
     }
   } else {
     switch (warps) {
-      case 1: return occupancy_kw<KIND, 1>(depth, table_smem, out);
-      case 2: return occupancy_kw<KIND, 2>(depth, table_smem, out);
-      case 4: return occupancy_kw<KIND, 4>(depth, table_smem, out);
-      case 8: return occupancy_kw<KIND, 8>(depth, table_smem, out);
-      case 16: return occupancy_kw<KIND, 16>(depth, table_smem, out);
-      case 32: return occupancy_kw<KIND, 32>(depth, table_smem, out);
+      case 1: return occupancy_kw<KIND, 1>(table_smem, out);
+      case 2: return occupancy_kw<KIND, 2>(table_smem, out);
+      case 4: return occupancy_kw<KIND, 4>(table_smem, out);
+      case 8: return occupancy_kw<KIND, 8>(table_smem, out);
+      case 16: return occupancy_kw<KIND, 16>(table_smem, out);
+      case 32: return occupancy_kw<KIND, 32>(table_smem, out);
     }
   }
   return -1;
@@ -493,12 +517,6 @@ bool warps_supported(uint32_t w) { return w == 1 || w == 2 || w == 4 || w == 8 |
 
 bool adaptive_warps_supported(uint32_t w) { return w == 4 || w == 8 || w == 16; }
 
-uint32_t adaptive_depth_class(uint32_t alphabet) {
-  if (alphabet <= 16) return 4;
-  if (alphabet <= 256) return 8;
-  return alphabet <= kMaxAdaptiveAlphabet ? 12 : 0;
-}
-
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   switch (kind) {
     case kPacked8: return launch_k<kPacked8>(a, grid, s);
@@ -506,17 +524,19 @@ cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cud
     case kGeneric16: return launch_k<kGeneric16>(a, grid, s);
     case kAdaptive8: return launch_k<kAdaptive8>(a, grid, s);
     case kAdaptive16: return launch_k<kAdaptive16>(a, grid, s);
+    case kAdaptive16Wide: return launch_k<kAdaptive16Wide>(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t depth, uint32_t table_smem, int* out) {
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out) {
   switch (kind) {
-    case kPacked8: return occupancy_k<kPacked8>(warps, depth, table_smem, out);
-    case kGeneric8: return occupancy_k<kGeneric8>(warps, depth, table_smem, out);
-    case kGeneric16: return occupancy_k<kGeneric16>(warps, depth, table_smem, out);
-    case kAdaptive8: return occupancy_k<kAdaptive8>(warps, depth, table_smem, out);
-    case kAdaptive16: return occupancy_k<kAdaptive16>(warps, depth, table_smem, out);
+    case kPacked8: return occupancy_k<kPacked8>(warps, table_smem, out);
+    case kGeneric8: return occupancy_k<kGeneric8>(warps, table_smem, out);
+    case kGeneric16: return occupancy_k<kGeneric16>(warps, table_smem, out);
+    case kAdaptive8: return occupancy_k<kAdaptive8>(warps, table_smem, out);
+    case kAdaptive16: return occupancy_k<kAdaptive16>(warps, table_smem, out);
+    case kAdaptive16Wide: return occupancy_k<kAdaptive16Wide>(warps, table_smem, out);
   }
   return -1;
 }

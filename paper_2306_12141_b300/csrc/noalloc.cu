@@ -125,14 +125,13 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
     a.kind = k;
     a.persistent = 1;
     a.table_smem = (uint32_t)((img.kind_smem[k] + 15) / 16 * 16);
-    a.depth = img.kind_depth[k];
+    a.warp_queue = img.kind_warp_queue[k];
     int per_sm = 0;
-    if (occupancy_ctas_per_sm(k, img.warps, a.depth, a.table_smem, &per_sm) != 0 || per_sm <= 0) {
+    if (occupancy_ctas_per_sm(k, img.warps, a.table_smem, &per_sm) != 0 || per_sm <= 0) {
       recoil_plan_free(plan);
       return fail(RECOIL_ECUDA, "occupancy query failed");
     }
-    const unsigned grid = (unsigned)std::min<uint64_t>(a.n_items, (uint64_t)per_sm * sms);
-    e = launch_decode(k, a, grid, cs);
+    e = launch_decode(k, a, launch_grid(a, per_sm, sms), cs);
   }
   // read the error flags back (this also makes the call return after the decode)
   DevControl ctl;

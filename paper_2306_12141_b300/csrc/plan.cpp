@@ -22,7 +22,10 @@ constexpr uint32_t kMaxSmem = 227 * 1024;
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 uint32_t table_kind_of(const Stream& s) {
-  if (s.adaptive()) return s.sym_bytes == 2 ? kAdaptive16 : kAdaptive8;
+  if (s.adaptive()) {
+    if (s.sym_bytes == 1) return kAdaptive8;
+    return s.alphabet() <= 256 ? kAdaptive16 : kAdaptive16Wide;
+  }
   if (s.sym_bytes == 2) return kGeneric16;
   if (s.n_bits <= 12 && !s.constant()) return kPacked8;
   return kGeneric8;
@@ -37,11 +40,10 @@ uint32_t adaptive_row_stride(uint32_t A) {
   return 2 * words;
 }
 
-uint32_t adaptive_depth(uint32_t A) {
-  uint32_t d = 0;
-  while ((1u << d) < A) d++;
-  return d;
-}
+uint32_t guide_bits(uint32_t n) { return std::min<uint32_t>(kGuideBits, n); }
+
+// Bytes between guide rows: 2^g + 1 entries, rounded up to 4.
+uint32_t guide_stride(uint32_t n) { return (uint32_t)align_up((1u << guide_bits(n)) + 1, 4); }
 
 // Decoder tables of a stream (built once and cached on the stream).
 const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_t* slot_bytes) {
@@ -50,16 +52,28 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
   const uint32_t k = table_kind_of(s);
   const uint32_t sb = (uint32_t)align_up((size_t)slots * 2, 16);
   if (s.table_img.empty()) {
-    if (k == kAdaptive8 || k == kAdaptive16) {
-      // one row per PDF: F(0..A) as 16-bit values, F(A) = 2^n kept modulo 2^16
+    if (is_adaptive_kind(k)) {
+      // one row per PDF: H(s) = F(s) - 1 modulo 2^16 for s = 0..A (H(0) = 0xffff,
+      // H(A) = 2^n - 1); guided kinds then add per row the symbol holding the
+      // first slot of each of the 2^g buckets (and of the last slot, entry 2^g)
       const uint32_t stride = adaptive_row_stride(A);
-      s.table_img.assign(align_up((size_t)s.n_tables * stride * 2, 16), 0);
+      const size_t rows_bytes = (size_t)s.n_tables * stride * 2;
+      const bool guided = adaptive_kind_guided(k);
+      const uint32_t gb = guide_bits(n), gstride = guide_stride(n);
+      s.table_img.assign(align_up(rows_bytes + (guided ? (size_t)s.n_tables * gstride : 0), 16), 0);
       uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data());
+      uint8_t* guide = s.table_img.data() + rows_bytes;
+      std::vector<uint32_t> F(A + 1);
       for (uint32_t t = 0; t < s.n_tables; t++) {
-        uint32_t F = 0;
-        for (uint32_t sym = 0; sym <= A; sym++) {
-          cdf[(size_t)t * stride + sym] = (uint16_t)F;
-          if (sym < A) F += s.freq[(size_t)t * A + sym];
+        F[0] = 0;
+        for (uint32_t sym = 0; sym < A; sym++) F[sym + 1] = F[sym] + s.freq[(size_t)t * A + sym];
+        for (uint32_t sym = 0; sym <= A; sym++) cdf[(size_t)t * stride + sym] = (uint16_t)(F[sym] - 1);
+        if (!guided) continue;
+        uint32_t sym = 0;
+        for (uint32_t b = 0; b <= (1u << gb); b++) {
+          const uint32_t slot = std::min<uint32_t>(b << (n - gb), (1u << n) - 1);
+          while (F[sym + 1] <= slot) sym++;              // the symbol whose slots hold `slot`
+          guide[(size_t)t * gstride + b] = (uint8_t)sym;
         }
       }
     } else if (k == kPacked8) {
@@ -152,12 +166,19 @@ struct recoil_plan {
   std::vector<uint64_t> word_off;                      // per stream, in words
   std::vector<uint64_t> tid_off;                       // per adaptive stream: its table numbers, in words
   uint32_t n_items = 0;
-  uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {}, kind_depth[kKinds] = {};
+  uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {}, kind_warp_queue[kKinds] = {};
   std::vector<uint32_t> stream_kind, stream_item_first, stream_item_count;
+  // shard plans (one stream): only entries [entry_first, entry_last) get work
+  // items; the others stay in the entry array as the previous-entry guards
+  // the decoders read. out_shift = first owned symbol (outputs start there).
+  bool shard = false;
+  uint32_t entry_first = 0, entry_last = 0;
+  uint64_t out_shift = 0;
 
   uint8_t* d_ws = nullptr;
   bool uploaded = false;
-  std::vector<void*> outs;
+  std::vector<void*> outs;                             // caller's output pointers
+  std::vector<void*> outs_dev;                         // as the kernels index them
   bool outs_on_device = false;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -213,37 +234,39 @@ static int plan_build(recoil_plan* P) {
       // the table numbers follow the words, one byte per symbol, on a chunk boundary
       d.tid = word_off;
       d.row_stride = adaptive_row_stride(s.alphabet());
-      d.depth = adaptive_depth(s.alphabet());
       d.n_tables = s.n_tables;
+      d.guide_stride = adaptive_kind_guided(kind) ? guide_stride(s.n_bits) : 0;
       P->tid_off[i] = word_off;
       word_off += align_up((s.n_syms + 1) / 2, kChunkWords);
     }
     P->kind_smem[kind] = std::max<uint32_t>(P->kind_smem[kind], d.table_bytes);
-    if (s.adaptive()) {
-      if (!adaptive_warps_supported(warps)) return fail(RECOIL_EINVAL, "adaptive streams decode with 4, 8 or 16 warps per CTA");
-      P->kind_depth[kind] = std::max(P->kind_depth[kind], adaptive_depth_class(s.alphabet()));
-    }
+    if (s.adaptive() && !adaptive_warps_supported(warps))
+      return fail(RECOIL_EINVAL, "adaptive streams decode with 4, 8 or 16 warps per CTA");
 
     const size_t first = entries.size();
     build_entries(s, i, entries);
+    size_t end_e = entries.size();
+    if (P->shard) {
+      end_e = first + P->entry_last;
+    }
     // a stream whose tables equal the previous stream's may fill up the
     // previous stream's last work item (one staged table serves both)
     const bool same_table = i > 0 && !per_stream && !items.empty() && items.back().kind == kind &&
                             P->streams[i - 1]->n_bits == s.n_bits && P->streams[i - 1]->sym_bytes == s.sym_bytes &&
                             P->streams[i - 1]->n_tables == s.n_tables && P->streams[i - 1]->freq == s.freq &&
                             items.back().it.entry + items.back().it.count == first;
-    size_t e = first;
-    if (same_table && items.back().it.count < warps) {
-      const uint32_t take = (uint32_t)std::min<size_t>(warps - items.back().it.count, entries.size() - e);
+    size_t e = first + (P->shard ? P->entry_first : 0);
+    if (same_table && !P->shard && items.back().it.count < warps) {
+      const uint32_t take = (uint32_t)std::min<size_t>(warps - items.back().it.count, end_e - e);
       items.back().it.count += take;
       for (uint32_t k = 0; k < take; k++) items.back().it.work = std::max(items.back().it.work, entry_work(entries[e + k]));
       e += take;
     }
-    for (; e < entries.size(); e += warps) {
+    for (; e < end_e; e += warps) {
       ItemK ik;
       ik.it.stream = i;
       ik.it.entry = (uint32_t)e;
-      ik.it.count = (uint32_t)std::min<size_t>(warps, entries.size() - e);
+      ik.it.count = (uint32_t)std::min<size_t>(warps, end_e - e);
       ik.it.work = 0;
       for (uint32_t k = 0; k < ik.it.count; k++) ik.it.work = std::max(ik.it.work, entry_work(entries[e + k]));
       ik.kind = kind;
@@ -253,6 +276,41 @@ static int plan_build(recoil_plan* P) {
   for (uint32_t k = 0; k < kKinds; k++) {
     if (P->kind_smem[k] + warps * ring_smem_per_warp() > kMaxSmem)
       return fail(RECOIL_EINVAL, "decoder tables too large for shared memory (alphabet or n too large)");
+  }
+  // Kinds whose items all decode with one table (one stream, or streams with
+  // identical models) are staged once per CTA; their entries become items of
+  // one entry each that warps pop on their own, so no warp waits at a CTA
+  // barrier for the slowest split of its item.
+  const Stream* table_of[kKinds] = {};
+  bool one_table[kKinds];
+  for (uint32_t k = 0; k < kKinds; k++) one_table[k] = !per_stream;
+  for (const ItemK& ik : items) {
+    const Stream* st = P->streams[ik.it.stream];
+    const Stream*& t = table_of[ik.kind];
+    if (!t) t = st;
+    else if (st != t && !(st->n_bits == t->n_bits && st->sym_bytes == t->sym_bytes && st->n_tables == t->n_tables &&
+                          st->freq == t->freq))
+      one_table[ik.kind] = false;
+  }
+  for (uint32_t k = 0; k < kKinds; k++) P->kind_warp_queue[k] = table_of[k] && one_table[k];
+  {
+    std::vector<ItemK> split;
+    split.reserve(items.size());
+    for (const ItemK& ik : items) {
+      if (!P->kind_warp_queue[ik.kind]) {
+        split.push_back(ik);
+        continue;
+      }
+      for (uint32_t j = 0; j < ik.it.count; j++) {
+        ItemK one = ik;
+        one.it.entry = ik.it.entry + j;
+        one.it.count = 1;
+        one.it.work = entry_work(entries[ik.it.entry + j]);
+        one.it.stream = entries[ik.it.entry + j].stream;
+        split.push_back(one);
+      }
+    }
+    items.swap(split);
   }
   // item order: by kind; persistent mode longest first, per-stream mode by stream
   const bool sort = !per_stream && !(P->opts.flags & RECOIL_BATCH_NO_SORT);
@@ -308,7 +366,7 @@ void plan_image(const recoil_plan* P, PlanImage* o) {
     o->kind_first[k] = P->kind_first[k];
     o->kind_count[k] = P->kind_count[k];
     o->kind_smem[k] = P->kind_smem[k];
-    o->kind_depth[k] = P->kind_depth[k];
+    o->kind_warp_queue[k] = P->kind_warp_queue[k];
   }
 }
 }  // namespace recoil
@@ -385,7 +443,6 @@ static int plan_launch(recoil_plan* P, cudaStream_t cs) {
       a.kind = k;
       a.persistent = 0;
       a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
-      a.depth = P->kind_depth[k];
       e = launch_decode(k, a, a.n_items, cs);
       if (e != cudaSuccess) return cuda_fail(e, "decode launch");
       P->launches++;
@@ -399,12 +456,12 @@ static int plan_launch(recoil_plan* P, cudaStream_t cs) {
     a.kind = k;
     a.persistent = 1;
     a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
-    a.depth = P->kind_depth[k];
+    a.warp_queue = P->kind_warp_queue[k];
     int per_sm = (int)P->opts.ctas_per_sm;
-    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, a.depth, a.table_smem, &per_sm) != 0)
+    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, a.table_smem, &per_sm) != 0)
       return fail(RECOIL_ECUDA, "occupancy query failed");
     if (per_sm <= 0) return fail(RECOIL_EINVAL, "kernel does not fit on an SM with these options");
-    const unsigned grid = (unsigned)std::min<uint64_t>(a.n_items, (uint64_t)per_sm * P->sms);
+    const unsigned grid = launch_grid(a, per_sm, P->sms);
     e = launch_decode(k, a, grid, cs);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     P->launches++;
@@ -472,9 +529,13 @@ int recoil_plan_decode(recoil_plan* P, void* const* d_outs, void* stream) {
   for (size_t i = 0; same && i < count; i++) same = P->outs[i] == d_outs[i];
   if (!same) {
     for (size_t i = 0; i < count; i++)
-      if (!d_outs[i] && P->streams[i]->n_syms) return fail(RECOIL_EINVAL, "null output buffer");
+      if (!d_outs[i] && P->streams[i]->n_syms && !(P->shard && P->n_items == 0))
+        return fail(RECOIL_EINVAL, "null output buffer");
     P->outs.assign(d_outs, d_outs + count);
-    cudaError_t e = cudaMemcpyAsync(P->d_ws + P->off_meta + P->off_outs, P->outs.data(), count * 8,
+    P->outs_dev = P->outs;
+    if (P->shard && count == 1 && P->outs_dev[0])  // the buffer starts at the first owned symbol
+      P->outs_dev[0] = (void*)((uintptr_t)P->outs_dev[0] - P->out_shift * P->streams[0]->sym_bytes);
+    cudaError_t e = cudaMemcpyAsync(P->d_ws + P->off_meta + P->off_outs, P->outs_dev.data(), count * 8,
                                     cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "output pointer upload");
     P->outs_on_device = true;
@@ -564,6 +625,50 @@ int recoil_shard(const recoil_stream* const* streams, uint32_t count, uint32_t w
     load[r] += bytes(i);
   }
   return RECOIL_OK;
+}
+
+int recoil_plan_create_shard(const recoil_stream* s, uint32_t world, uint32_t rank, const recoil_batch_opts* opts,
+                             recoil_plan** out, uint64_t* sym_lo, uint64_t* sym_hi) {
+  clear_error();
+  if (!s || !out || !sym_lo || !sym_hi || world < 1 || rank >= world)
+    return fail(RECOIL_EINVAL, "null argument, world < 1 or rank >= world");
+  if (opts && opts->split_symbols) return fail(RECOIL_EINVAL, "combine the stream before sharding (split_symbols must be 0)");
+  *out = nullptr;
+  try {
+    // owned ranges of the kept entries: entry k owns [m_{k-1}, m_k), the final one up to N
+    std::vector<DevEntry> ents;
+    build_entries(*s, 0, ents);
+    const uint32_t K = (uint32_t)ents.size();
+    // run boundaries: rank r starts at the first entry whose owned range ends
+    // past r * N / world (contiguous, monotone, every entry in exactly one run)
+    auto start_of = [&](uint32_t r) -> uint32_t {
+      if (r == 0) return 0;
+      if (r >= world) return K;
+      const uint64_t target = (uint64_t)s->n_syms * r / world;
+      uint32_t k = 0;
+      while (k < K && (uint64_t)ents[k].hi1 <= target) k++;
+      return k;
+    };
+    const uint32_t first = start_of(rank), last = start_of(rank + 1);
+    *sym_lo = first < K ? ents[first].lo : s->n_syms;
+    *sym_hi = last < K ? ents[last].lo : s->n_syms;
+    if (first >= last) *sym_hi = *sym_lo;
+    std::unique_ptr<recoil_plan> P(new recoil_plan());
+    if (opts) P->opts = *opts;
+    P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta : 16;
+    if (!warps_supported(P->warps)) return fail(RECOIL_EINVAL, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
+    P->streams.push_back(s);
+    P->shard = true;
+    P->entry_first = first;
+    P->entry_last = std::max(first, last);
+    P->out_shift = *sym_lo;
+    int rc = plan_build(P.get());
+    if (rc) return rc;
+    *out = P.release();
+    return RECOIL_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(RECOIL_ENOMEM, "host allocation failed");
+  }
 }
 
 int recoil_decode(const recoil_stream* s, void* d_out, void* d_ws, size_t ws_bytes, void* stream) {

@@ -28,10 +28,18 @@ enum TableKind : uint32_t {
   kPacked8 = 0,    // 8-bit symbols, n <= 12, f < 4096: one u32 per slot = bias | sym << 12 | f << 20
   kGeneric8 = 1,   // 8-bit symbols otherwise: u16 slot -> symbol, u32 symbol -> (f-1) << 16 | F
   kGeneric16 = 2,  // 16-bit symbols: same tables as kGeneric8, 16-bit stores
-  kAdaptive8 = 3,  // adaptive model (a PDF row per symbol index), 8-bit symbols: u16 CDF rows
-  kAdaptive16 = 4, // adaptive model, 16-bit symbols
-  kKinds = 5,
+  // adaptive model (a PDF row per symbol index): one u16 CDF row per PDF
+  kAdaptive8 = 3,       // 8-bit symbols; a bucket guide per row narrows the search
+  kAdaptive16 = 4,      // 16-bit symbols, alphabet <= 256; bucket guide
+  kAdaptive16Wide = 5,  // 16-bit symbols, alphabet <= 4096; 12-step binary search
+  kKinds = 6,
 };
+
+__host__ __device__ constexpr bool is_adaptive_kind(uint32_t k) { return k >= kAdaptive8 && k < kKinds; }
+// Kinds whose rows come with a bucket guide (alphabets up to 256: one byte per bucket).
+__host__ __device__ constexpr bool adaptive_kind_guided(uint32_t k) { return k == kAdaptive8 || k == kAdaptive16; }
+// The guide of a row: 2^g buckets over the 2^n slots, g = min(8, n).
+constexpr uint32_t kGuideBits = 8;
 
 // Longest alphabet of an adaptive model (the decoder's CDF search covers 2^12 symbols).
 constexpr uint32_t kMaxAdaptiveAlphabet = 4096;
@@ -98,8 +106,8 @@ struct alignas(16) DevStream {
   uint32_t table_bytes;      // bytes of the table image (multiple of 16)
   uint32_t slot_bytes;       // generic kinds: bytes of the slot -> symbol part (multiple of 16)
   uint32_t row_stride;       // adaptive: 16-bit entries between CDF rows (odd number of 32-bit words)
-  uint32_t depth;            // adaptive: steps of the CDF search, ceil(log2(alphabet))
   uint32_t n_tables;         // adaptive: CDF rows
+  uint32_t guide_stride;     // guided adaptive kinds: bytes between guide rows (after all CDF rows)
 };
 static_assert(sizeof(DevStream) == 64, "DevStream layout");
 
@@ -140,16 +148,22 @@ struct LaunchArgs {
   DevControl* control;
   uint32_t table_smem;       // bytes reserved for tables in shared memory
   uint32_t warps;            // warps per CTA
-  uint32_t depth;            // adaptive kinds: CDF search steps of the launch (4, 8 or 12)
+  uint32_t warp_queue;       // 1: every item is one entry and all share one table; warps pop items alone
 };
+
+// Grid of a persistent launch: enough CTAs for the items, at most the resident ones.
+inline unsigned launch_grid(const LaunchArgs& a, int ctas_per_sm, int sms) {
+  const uint64_t need = a.warp_queue ? (a.n_items + a.warps - 1) / a.warps : a.n_items;
+  const uint64_t cap = (uint64_t)ctas_per_sm * (uint64_t)sms;
+  return (unsigned)(need < cap ? need : cap);
+}
 
 // Kernel launchers (decode_kernels.cu).
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s);
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t depth, uint32_t table_smem, int* out);
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out);
 size_t ring_smem_per_warp();
 bool warps_supported(uint32_t warps);   // CTA sizes the kernels are built for: 1, 2, 4, 8, 16, 32 warps
 bool adaptive_warps_supported(uint32_t warps);   // adaptive kinds: 4, 8, 16 warps
-uint32_t adaptive_depth_class(uint32_t alphabet); // CDF search steps built for an alphabet (0: too large)
 
 // Host images of a plan (plan.cpp), for entry points that place them in
 // device memory of their own. meta = control, output pointers, stream
@@ -162,7 +176,7 @@ struct PlanImage {
   size_t table_bytes;
   size_t ws_off_tables;      // workspace offset of the tables (words start at 0)
   uint32_t warps;
-  uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds], kind_depth[kKinds];
+  uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds], kind_warp_queue[kKinds];
 };
 }  // namespace recoil
 struct recoil_plan;

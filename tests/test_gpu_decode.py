@@ -322,3 +322,46 @@ def test_partitions_sharing_one_model(recoil_lib, warps):
     streams = [R.encode_with_table(p, 12, f, 1 + len(p) // 40_000) for p in parts]
     outs = gpu_decode(R, streams, {"warps_per_cta": warps})
     assert np.array_equal(np.concatenate(outs), s)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8, 100])
+def test_shard_plans_tile_one_stream(recoil_lib, world):
+    """recoil_plan_create_shard: each rank's run decodes into a buffer of its own range only;
+    the ranks run one after another on this GPU and their ranges concatenate to the stream."""
+    R = recoil_lib
+    st = workloads.Stream("zipf", 2_000_003, 1, 12, "zipf", {"s": 1.2}, seed=81)
+    s = st.symbols()
+    p = R.combine_splits(R.encode_with_splits(s, st.n_bits, 512), 64)
+    pieces, prev_hi = [], 0
+    for r in range(world):
+        plan, lo, hi = R.Plan.shard(p, world, r, {"warps_per_cta": 8})
+        assert lo == prev_hi
+        prev_hi = hi
+        ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device="cuda")
+        buf = torch.full((max(1, hi - lo) + 64,), 0xAB, dtype=torch.uint8, device="cuda")
+        plan.upload(ws)
+        plan.decode([buf.data_ptr()])
+        assert plan.errors() == 0
+        b = buf.cpu().numpy()
+        assert np.all(b[hi - lo:] == 0xAB)                   # nothing written past the range
+        pieces.append(b[:hi - lo])
+    assert prev_hi == len(s)
+    assert np.array_equal(np.concatenate(pieces), s)
+
+
+def test_shard_plans_adaptive_stream(recoil_lib):
+    R = recoil_lib
+    a = workloads.AdaptiveStream("t", 1_000_003, seed=82)
+    tables = a.tables()
+    s, tid = a.draw()
+    p = R.encode_adaptive(s, a.n_bits, tables, tid, 300)
+    pieces = []
+    for r in range(4):
+        plan, lo, hi = R.Plan.shard(p, 4, r, {"warps_per_cta": 16})
+        ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device="cuda")
+        buf = torch.zeros(max(1, 2 * (hi - lo)), dtype=torch.uint8, device="cuda")
+        plan.upload(ws)
+        plan.decode([buf.data_ptr()])
+        assert plan.errors() == 0
+        pieces.append(buf.cpu().numpy()[: 2 * (hi - lo)].view(np.uint16))
+    assert np.array_equal(np.concatenate(pieces), s)
