@@ -414,7 +414,7 @@ def run_adaptive(a):
     tables = st.tables()
     s, tid = st.draw()
     enc = R.encode_adaptive(s, st.n_bits, tables, tid, max(1, min(65536, len(s) // 4096)))
-    warps = a.warps or 8
+    warps = a.warps or 16
     cs = torch.cuda.Stream(device=dev)
     out = torch.empty(len(s) * 2, dtype=torch.uint8, device=dev)
     ref = torch.from_numpy(s.view(np.uint8)).to(dev)
@@ -488,8 +488,9 @@ def run_adaptive(a):
                        "compressed_bytes": 2 * c.info["n_words"] + 4 * 32, "table_number_bytes": len(s),
                        "l2": "inputs larger than L2 (no flush)", "scale": a.scale},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
-                         "kernel": "decode_kernel<kAdaptive16>",
+                         "frac": achieved / peaks["hbm_gbs"],
+                         "traffic": recorded_traffic(f"adaptive w{warps} k{a.splits}") if a.scale == 1.0 else None,
+                         "peak_source": peaks["source"], "kernel": "decode_kernel<kAdaptive16>",
                          "bytes": "compressed words + table numbers in, symbols out"},
             "clocks": clocks, "gpu_launches": launches * a.steps, "e2e": e2e, "split_sweep_gbs": sweep}
     if not a.no_cpu:
