@@ -539,7 +539,16 @@ def run_ours(a):
         warps = a.warps or (8 if batch else 16)
     opts = {"warps_per_cta": warps, "ctas_per_sm": a.ctas_per_sm, "split_symbols": split_symbols,
             "flags": R.BATCH_GRAPH}
+    t_host = time.perf_counter()
     plan = R.Plan(streams, opts)
+    plan_ms = (time.perf_counter() - t_host) * 1e3       # host: combining (Sec. 3.3) + descriptors
+    combine_us = None
+    if not batch:
+        reps = 20
+        t_host = time.perf_counter()
+        for _ in range(reps):
+            R.combine_splits(encoded[0], a.splits)
+        combine_us = (time.perf_counter() - t_host) / reps * 1e6
     ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -658,6 +667,8 @@ def run_ours(a):
                    "splits": sum(st.info["n_entries"] for st in plan.streams) if not batch else None,
                    "split_symbols": split_symbols, "warps_per_cta": opts["warps_per_cta"],
                    "autotuned": tuned,
+                   "host_plan_ms": round(plan_ms, 3),
+                   "host_combine_us": round(combine_us, 1) if combine_us is not None else None,
                    "parallelism": f"weak x{world}", "l2": "inputs larger than L2 (no flush)",
                    "scale": a.scale},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

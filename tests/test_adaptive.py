@@ -193,3 +193,93 @@ def test_gpu_adaptive_full_size_sampled(recoil_lib):
         lo, hi = oracle.owned_range(st, int(k))
         ref = oracle.decode_thread(st, int(k))
         assert np.array_equal(out[lo:hi + 1], ref[lo:hi + 1].astype(np.uint16)), k
+
+
+def _adaptive_pool(R, count, seed):
+    g = np.random.default_rng(seed)
+    syms, streams = [], []
+    for k in range(count):
+        N = int(g.integers(1, 300_000))
+        if k % 3 == 2:
+            st = workloads.Stream("l", N, 1, 12, "laplace", {"mean": 128.0, "scale": float(g.uniform(2, 64))},
+                                  seed=seed + k)
+            s = st.symbols()
+            streams.append(R.encode_with_splits(s, st.n_bits, max(1, N // 4096)))
+        else:
+            cfg = CASES[k % len(CASES)]
+            a, tables, s, tid = _case(N, seed + k, **cfg)
+            streams.append(R.encode_adaptive(s, cfg["n_bits"], tables, tid, max(1, N // 4096)))
+        syms.append(s)
+    return syms, streams
+
+
+@pytest.mark.gpu
+def test_gpu_adaptive_in_serving_pipeline_and_autotune(recoil_lib, tmp_path):
+    """Adaptive streams next to static ones through the serving runtime, the host-to-host
+    pipeline and the autotuner: every output is the input."""
+    import torch
+    R = recoil_lib
+    syms, pool = _adaptive_pool(R, 18, 60)
+    cs = torch.cuda.current_stream()
+    # serving: Poisson arrivals over the mixed pool
+    n_req = 200
+    picks = workloads.request_picks(len(pool), n_req, seed=61)
+    arrive = workloads.poisson_arrivals(20_000.0, n_req, seed=61)
+    outs = [torch.full((max(1, len(syms[p]) * syms[p].itemsize),), 0xAB, dtype=torch.uint8, device="cuda")
+            for p in picks]
+    budget = 64 << 20
+    need = R.serve_arena_size(pool, budget, warps_per_cta=8)
+    arena = torch.empty(need, dtype=torch.uint8, device="cuda")
+    res, stats = R.serve(pool, picks, arrive, arena, need, budget, outs=[o.data_ptr() for o in outs],
+                         warps_per_cta=8, max_inflight=4, max_batch=16, timeout_s=60.0)
+    assert stats["requests"] == n_req
+    for r, p in enumerate(picks):
+        s = syms[p]
+        assert np.array_equal(outs[r].cpu().numpy()[: len(s) * s.itemsize].view(s.dtype), s), r
+    # host to host
+    for st in pool:
+        R.stream_pin(st)
+    pipe = R.Pipeline(pool, {"warps_per_cta": 8, "split_symbols": 32768}, groups=3)
+    wsb, stb = pipe.sizes
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    stage = torch.empty(stb, dtype=torch.uint8, device="cuda")
+    host = [torch.full((max(1, len(s) * s.itemsize),), 0xAB, dtype=torch.uint8, pin_memory=True) for s in syms]
+    s2 = torch.cuda.Stream()
+    pipe.run([h.data_ptr() for h in host], ws, wsb, stage, stb, s2)
+    s2.synchronize()
+    assert pipe.errors() == 0
+    for s, h in zip(syms, host):
+        assert np.array_equal(h.numpy()[: len(s) * s.itemsize].view(s.dtype), s)
+    # autotuner
+    need = R.autotune_workspace_size(pool)
+    tws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    touts = [torch.zeros(max(1, len(s) * s.itemsize), dtype=torch.uint8, device="cuda") for s in syms]
+    best, ms = R.autotune(pool, [o.data_ptr() for o in touts], tws, need, cs, steps=2,
+                          cache_path=str(tmp_path / "tune.txt"))
+    assert best["warps_per_cta"] in (4, 8, 16) and ms > 0
+    for s, o in zip(syms, touts):
+        assert np.array_equal(o.cpu().numpy()[: len(s) * s.itemsize].view(s.dtype), s)
+
+
+@pytest.mark.gpu
+def test_gpu_adaptive_corrupt_words_flagged(recoil_lib):
+    """Words flipped in the uploaded device image of an adaptive stream are reported by
+    the decoders' state cross-check (no fault, no hang), and the context stays usable."""
+    import torch
+    R = recoil_lib
+    a, tables, s, tid = _case(200_000, 70)
+    p = R.encode_adaptive(s, 16, tables, tid, 8)
+    nw = p.info["n_words"]
+    out = torch.zeros(2 * len(s), dtype=torch.uint8, device="cuda")
+    plan = R.Plan([p], {"warps_per_cta": 8})
+    ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    torch.cuda.synchronize()
+    words = ws[: 2 * nw].view(torch.int16)                # the first stream's words start the workspace
+    words[nw // 3: nw // 3 + 40] ^= 0x5A5A
+    plan.decode([out.data_ptr()])
+    assert plan.errors() != 0
+    plan.upload(ws)                                       # a clean image: exact again
+    plan.decode([out.data_ptr()])
+    assert plan.errors() == 0
+    assert np.array_equal(out.cpu().numpy().view(np.uint16), s)
