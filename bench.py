@@ -64,7 +64,7 @@ def _args():
                     help="zipf: split counts to sweep (empty to skip)")
     ap.add_argument("--soak", type=float, default=1.0, help="seconds of untimed steps while sampling clocks")
     ap.add_argument("--serve-rate", type=float, default=10000.0, help="batch: serving check at this request rate")
-    ap.add_argument("--e2e-groups", type=int, default=8, help="stream groups of the end-to-end pipeline")
+    ap.add_argument("--e2e-groups", type=int, default=16, help="stream groups of the end-to-end pipeline")
     ap.add_argument("--serve-requests", type=int, default=5000, help="batch: requests in the serving check (0: skip)")
     return ap.parse_args()
 

@@ -311,10 +311,12 @@ typedef struct recoil_pipeline recoil_pipeline;   /* opaque: grouped plans + cop
 /*
  * Prepare host-to-host decoding of `count` streams with copy/compute overlap:
  * the streams are cut into `groups` (0 = 8) groups of about equal output
- * bytes, each with its own plan (opts as for recoil_plan_create) and page-
- * locked copies of its descriptors and tables. For full link speed pin the
- * streams' words first (recoil_stream_pin). The streams must outlive the
- * pipeline. Errors: EINVAL, ENOMEM, ECUDA.
+ * bytes, each with its own plan (opts as for recoil_plan_create), a page-
+ * locked copy of its descriptors and a page-locked image of its words, table
+ * numbers and tables as they lie in the workspace (so a group is copied in
+ * with two copies; the pipeline holds about the streams' compressed size in
+ * page-locked host memory). The streams must outlive the pipeline.
+ * Errors: EINVAL, ENOMEM, ECUDA.
  */
 int recoil_pipeline_create(const recoil_stream* const* streams, uint32_t count, const recoil_batch_opts* opts,
                            uint32_t groups, recoil_pipeline** out);
@@ -324,7 +326,8 @@ int recoil_pipeline_sizes(const recoil_pipeline* p, size_t* ws_bytes, size_t* st
 
 /*
  * Decode every stream into host memory: h_outs[i] receives n_syms * sym_bytes
- * bytes (page-locked for full link speed). Per group, on three internal CUDA
+ * bytes (page-locked for full link speed; buffers of consecutive streams that
+ * follow each other in memory are copied out together). Per group, on three internal CUDA
  * streams: copy the group in, decode it, copy its symbols out, so copies in
  * both directions overlap the decoding of other groups. The run starts after
  * work already queued on cuda_stream and cuda_stream waits for its end, so

@@ -2,7 +2,12 @@
 //
 // The streams are cut into groups of about equal output bytes; each group has
 // its own plan and its own region of the workspace and of the device staging
-// buffer. One run queues, per group g,
+// buffer. At creation each group's words, table numbers and tables are laid
+// out in one page-locked image of its workspace region, so a run copies a
+// group in with two copies (that image and the descriptors), and copies its
+// symbols out with one copy per run of members whose host buffers follow
+// each other (the staging packs the outputs back to back). One run queues,
+// per group g,
 //   copy-in stream:  descriptors, tables and words of g (page-locked sources)
 //   compute stream:  the persistent decode of g, after g's copy-in
 //   copy-out stream: the decoded symbols of g to the caller's host buffers
@@ -34,8 +39,8 @@ struct Group {
   std::vector<size_t> out_off;       // per member, inside the group's staging
   uint8_t* meta = nullptr;           // page-locked copies of the plan's descriptors and tables
   size_t meta_bytes = 0, off_meta = 0, off_outs = 0;
-  uint8_t* tables = nullptr;
-  size_t table_bytes = 0, off_tables = 0;
+  uint8_t* bulk = nullptr;           // page-locked image of the bulk region (words, table numbers, tables)
+  size_t bulk_bytes = 0;
   cudaEvent_t in = nullptr, dec = nullptr, out = nullptr;
   bool used = false;
   uint8_t* bound_ws = nullptr;       // workspace region the plan was last bound to
@@ -57,7 +62,7 @@ struct recoil_pipeline {
     for (Group& g : groups) {
       if (g.plan) recoil_plan_free(g.plan);
       if (g.meta) cudaFreeHost(g.meta);
-      if (g.tables) cudaFreeHost(g.tables);
+      if (g.bulk) cudaFreeHost(g.bulk);
       for (cudaEvent_t e : {g.in, g.dec, g.out})
         if (e) cudaEventDestroy(e);
     }
@@ -107,23 +112,24 @@ int recoil_pipeline_create(const recoil_stream* const* streams, uint32_t count, 
       G.ws_off = P->ws_bytes;
       P->ws_bytes += align_up(G.ws_bytes, kAlign);
       G.stage_off = P->stage_bytes;
-      for (uint32_t i : G.members) {
+      for (uint32_t i : G.members) {                 // back to back, each on its element size
+        G.stage_bytes = align_up(G.stage_bytes, streams[i]->sym_bytes);
         G.out_off.push_back(G.stage_bytes);
-        G.stage_bytes += align_up(std::max<size_t>(1, P->out_bytes[i]), kAlign);
+        G.stage_bytes += P->out_bytes[i];
       }
+      G.stage_bytes = align_up(std::max<size_t>(1, G.stage_bytes), kAlign);
       P->stage_bytes += G.stage_bytes;
       PlanImage img;
       plan_image(G.plan, &img);
       G.meta_bytes = img.meta_bytes;
       G.off_meta = plan_bulk_bytes(G.plan);
       G.off_outs = img.off_outs;
-      G.table_bytes = img.table_bytes;
-      G.off_tables = img.ws_off_tables;
+      G.bulk_bytes = plan_bulk_bytes(G.plan);
       if (e == cudaSuccess) e = cudaHostAlloc((void**)&G.meta, std::max<size_t>(1, G.meta_bytes), cudaHostAllocDefault);
-      if (e == cudaSuccess) e = cudaHostAlloc((void**)&G.tables, std::max<size_t>(1, G.table_bytes), cudaHostAllocDefault);
+      if (e == cudaSuccess) e = cudaHostAlloc((void**)&G.bulk, std::max<size_t>(1, G.bulk_bytes), cudaHostAllocDefault);
       if (e != cudaSuccess) break;
       std::memcpy(G.meta, img.meta, G.meta_bytes);
-      std::memcpy(G.tables, img.tables, G.table_bytes);
+      plan_bulk_image(G.plan, G.bulk);
       for (cudaEvent_t* ev : {&G.in, &G.dec, &G.out})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     }
@@ -174,10 +180,8 @@ int recoil_pipeline_run(recoil_pipeline* P, void* const* h_outs, void* d_ws, siz
     // copy-in, once the previous run's decode of this group is done with the region
     if (G.used) e = cudaStreamWaitEvent(P->s_in, G.dec, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(gws + G.off_meta, G.meta, G.meta_bytes, cudaMemcpyHostToDevice, P->s_in);
-    if (e == cudaSuccess && G.table_bytes)
-      e = cudaMemcpyAsync(gws + G.off_tables, G.tables, G.table_bytes, cudaMemcpyHostToDevice, P->s_in);
-    const std::vector<const Stream*>& ss = plan_streams(G.plan);
-    for (size_t k = 0; k < ss.size() && e == cudaSuccess; k++) e = plan_upload_stream(G.plan, k, gws, P->s_in);
+    if (e == cudaSuccess && G.bulk_bytes)
+      e = cudaMemcpyAsync(gws, G.bulk, G.bulk_bytes, cudaMemcpyHostToDevice, P->s_in);
     if (e == cudaSuccess) e = cudaEventRecord(G.in, P->s_in);
     if (e != cudaSuccess) break;
     // decode, once the copy-in is there and the previous copy-out left the staging
@@ -198,10 +202,18 @@ int recoil_pipeline_run(recoil_pipeline* P, void* const* h_outs, void* d_ws, siz
     e = cudaEventRecord(G.dec, P->s_comp);
     // copy-out
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_out, G.dec, 0);
-    for (size_t k = 0; k < G.members.size() && e == cudaSuccess; k++) {
+    for (size_t k = 0; k < G.members.size() && e == cudaSuccess;) {
+      // one copy for each run of members that follow each other on both sides
       const uint32_t i = G.members[k];
-      if (!P->out_bytes[i]) continue;
-      e = cudaMemcpyAsync(h_outs[i], outs[k], P->out_bytes[i], cudaMemcpyDeviceToHost, P->s_out);
+      size_t bytes = P->out_bytes[i], j = k + 1;
+      while (j < G.members.size()) {
+        const uint32_t n = G.members[j];
+        if ((uint8_t*)h_outs[n] != (uint8_t*)h_outs[i] + bytes || G.out_off[j] != G.out_off[k] + bytes) break;
+        bytes += P->out_bytes[n];
+        j++;
+      }
+      if (bytes) e = cudaMemcpyAsync(h_outs[i], outs[k], bytes, cudaMemcpyDeviceToHost, P->s_out);
+      k = j;
     }
     if (e == cudaSuccess) e = cudaEventRecord(G.out, P->s_out);
     G.used = true;

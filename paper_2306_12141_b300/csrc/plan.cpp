@@ -387,6 +387,16 @@ cudaError_t plan_upload_stream(const recoil_plan* P, size_t i, uint8_t* ws, cuda
 }
 
 size_t plan_bulk_bytes(const recoil_plan* P) { return P->off_meta; }
+
+void plan_bulk_image(const recoil_plan* P, uint8_t* dst) {
+  std::memset(dst, 0, P->off_meta);
+  for (size_t i = 0; i < P->streams.size(); i++) {
+    const Stream& s = *P->streams[i];
+    if (s.n_words()) std::memcpy(dst + P->word_off[i] * 2, s.word_data(), s.n_words() * 2);
+    if (s.adaptive() && s.n_syms) std::memcpy(dst + P->tid_off[i] * 2, s.tid->data(), s.n_syms);
+  }
+  if (!P->tables.empty()) std::memcpy(dst + P->off_tables, P->tables.data(), P->tables.size());
+}
 const std::vector<const Stream*>& plan_streams(const recoil_plan* P) { return P->streams; }
 
 int plan_upload_parts(recoil_plan* P, void* d_ws, size_t ws_bytes, cudaStream_t cs, bool bulk, bool meta) {

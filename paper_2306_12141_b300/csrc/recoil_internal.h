@@ -192,6 +192,9 @@ size_t plan_bulk_bytes(const recoil_plan* plan);
 const std::vector<const Stream*>& plan_streams(const recoil_plan* plan);
 // Copy stream k's bulk data (words; table numbers of an adaptive stream) to its place in ws.
 cudaError_t plan_upload_stream(const recoil_plan* plan, size_t k, uint8_t* ws, cudaStream_t s);
+// Host image of the bulk region (words, table numbers, tables) exactly as it
+// sits at the start of the workspace: plan_bulk_bytes bytes written to dst.
+void plan_bulk_image(const recoil_plan* plan, uint8_t* dst);
 
 // Error reporting (thread-local message).
 int fail(int code, const std::string& msg);
