@@ -215,9 +215,12 @@ def oracle_rate(specs, syms, seconds: float, threads: int, seed: int = 0):
 def cpu_baseline(specs, syms, seconds: float) -> dict:
     threads = os.cpu_count() or 1
     v, picked, done = oracle_rate(specs, syms, seconds, threads)
+    v1, picked1, done1 = oracle_rate(specs, syms, max(1.0, seconds / 4), 1, seed=1)
     return {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle",
             "sample": f"{picked} of {len(specs)} batch streams ({done / 1e6:.1f} MB of symbols); oracle "
-                      f"interleaved decoder (plain C -O2), one instance per host thread, decode wall time"}
+                      f"interleaved decoder (plain C -O2), one instance per host thread, decode wall time",
+            "single_core": {"value": v1, "unit": "GB/s", "cores": 1,
+                            "sample": f"{picked1} streams ({done1 / 1e6:.1f} MB), one thread"}}
 
 
 def run_reference(a):
