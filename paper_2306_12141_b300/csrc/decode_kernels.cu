@@ -424,15 +424,19 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlock
     return;
   }
 
-  // CTA items of up to WARPS entries; the table is restaged when the stream changes
+  // CTA items: up to WARPS entries of one stream (or of streams sharing one
+  // table); the table is restaged when the stream changes and the warps pop
+  // the item's entries from a shared counter
+  __shared__ uint32_t s_next;
   uint32_t staged = 0xffffffffu;
   uint32_t it = blockIdx.x;
   for (;;) {
     if (a.persistent) {
       if (threadIdx.x == 0) s_item = atomicAdd(&a.control->head[a.kind], 1u);
-      __syncthreads();
-      it = s_item;
     }
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    if (a.persistent) it = s_item;
     if (it >= a.n_items) break;
     const DevItem item = a.items[it];
     const DevStream& st = a.streams[item.stream];
@@ -441,7 +445,13 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlock
       staged = item.stream;
       __syncthreads();
     }
-    if ((uint32_t)warp < item.count) decode_entry(st, item.entry + warp);
+    for (;;) {
+      uint32_t k = 0;
+      if ((threadIdx.x & 31) == 0) k = atomicAdd(&s_next, 1u);
+      k = __shfl_sync(kFull, k, 0);
+      if (k >= item.count) break;
+      decode_entry(st, item.entry + k);
+    }
     if (!a.persistent) break;
     __syncthreads();
   }

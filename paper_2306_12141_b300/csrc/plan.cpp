@@ -256,17 +256,20 @@ static int plan_build(recoil_plan* P) {
                             P->streams[i - 1]->n_tables == s.n_tables && P->streams[i - 1]->freq == s.freq &&
                             items.back().it.entry + items.back().it.count == first;
     size_t e = first + (P->shard ? P->entry_first : 0);
-    if (same_table && !P->shard && items.back().it.count < warps) {
-      const uint32_t take = (uint32_t)std::min<size_t>(warps - items.back().it.count, end_e - e);
+    // items of one CTA round: longer items (several rounds) leave longer tails
+    // at the end of the queue and measured much slower on uneven batches
+    const uint32_t cap = warps;
+    if (same_table && !P->shard && items.back().it.count < cap) {
+      const uint32_t take = (uint32_t)std::min<size_t>(cap - items.back().it.count, end_e - e);
       items.back().it.count += take;
       for (uint32_t k = 0; k < take; k++) items.back().it.work = std::max(items.back().it.work, entry_work(entries[e + k]));
       e += take;
     }
-    for (; e < end_e; e += warps) {
+    for (; e < end_e; e += cap) {
       ItemK ik;
       ik.it.stream = i;
       ik.it.entry = (uint32_t)e;
-      ik.it.count = (uint32_t)std::min<size_t>(warps, end_e - e);
+      ik.it.count = (uint32_t)std::min<size_t>(cap, end_e - e);
       ik.it.work = 0;
       for (uint32_t k = 0; k < ik.it.count; k++) ik.it.work = std::max(ik.it.work, entry_work(entries[e + k]));
       ik.kind = kind;

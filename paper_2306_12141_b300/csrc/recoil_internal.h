@@ -111,12 +111,13 @@ struct alignas(16) DevStream {
 };
 static_assert(sizeof(DevStream) == 64, "DevStream layout");
 
-// A unit of work for one CTA: up to warps_per_cta consecutive entries, of one
-// stream or of consecutive streams whose decoder tables are identical.
+// A unit of work for one CTA: consecutive entries of one stream or of
+// consecutive streams whose decoder tables are identical; the CTA's warps pop
+// them one at a time.
 struct alignas(16) DevItem {
   uint32_t stream;
   uint32_t entry;            // first DevEntry
-  uint32_t count;            // number of entries (<= warps per CTA)
+  uint32_t count;            // number of entries
   uint32_t work;             // estimated symbols decoded (for ordering)
 };
 
