@@ -420,7 +420,7 @@ def run_adaptive(a):
     tables = st.tables()
     s, tid = st.draw()
     enc = R.encode_adaptive(s, st.n_bits, tables, tid, max(1, min(65536, len(s) // 4096)))
-    warps = a.warps or 16
+    warps = a.warps                                    # 0: the library picks the CTA size
     cs = torch.cuda.Stream(device=dev)
     out = torch.empty(len(s) * 2, dtype=torch.uint8, device=dev)
     ref = torch.from_numpy(s.view(np.uint8)).to(dev)
@@ -450,6 +450,7 @@ def run_adaptive(a):
             del sws
         c = R.combine_splits(enc, a.splits)
         plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+        warps = plan.warps_per_cta
         ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
         plan.upload(ws, stream=cs)
         decode = lambda: plan.decode([out.data_ptr()], cs)  # noqa: E731
@@ -542,12 +543,13 @@ def run_ours(a):
         del tws
     else:
         split_symbols = (65536 if a.split_symbols < 0 else a.split_symbols) if batch else 0
-        warps = a.warps or (8 if batch else 16)
+        warps = a.warps or (8 if batch else 0)         # 0: the library picks the CTA size from the split count
     opts = {"warps_per_cta": warps, "ctas_per_sm": a.ctas_per_sm, "split_symbols": split_symbols,
             "flags": R.BATCH_GRAPH}
     t_host = time.perf_counter()
     plan = R.Plan(streams, opts)
     plan_ms = (time.perf_counter() - t_host) * 1e3       # host: combining (Sec. 3.3) + descriptors
+    opts["warps_per_cta"] = warps = plan.warps_per_cta
     combine_us = None
     if not batch:
         reps = 20
@@ -616,7 +618,7 @@ def run_ours(a):
             sweep = {}
             for k in a.sweep:
                 c = R.combine_splits(encoded[0], k)
-                sp = R.Plan([c], {"warps_per_cta": opts["warps_per_cta"], "flags": R.BATCH_GRAPH})
+                sp = R.Plan([c], {"warps_per_cta": a.warps, "flags": R.BATCH_GRAPH})
                 sws = torch.empty(sp.workspace_size, dtype=torch.uint8, device=dev)
                 sp.upload(sws, stream=cs)
                 t = timed(lambda: sp.decode(out_ptrs, cs), 5, 2)

@@ -203,7 +203,9 @@ const char* recoil_last_error(void);
 
 /* Batch options. Zero fields take defaults (or the autotuned values). */
 typedef struct {
-  uint32_t warps_per_cta;    /* decoder warps per CTA (4, 8, 16, 32); default 16 */
+  uint32_t warps_per_cta;    /* decoder warps per CTA (1, 2, 4, 8, 16, 32; adaptive streams 4, 8, 16);
+                                0 = about one CTA round of splits per SM: the power of two
+                                below splits / SMs, clamped to [4, 16] */
   uint32_t ctas_per_sm;      /* persistent CTAs per SM; default: occupancy maximum */
   uint32_t split_symbols;    /* combine each stream to ceil(N / split_symbols) splits; 0 = keep all */
   uint32_t flags;            /* RECOIL_BATCH_* */
@@ -252,6 +254,9 @@ int recoil_plan_errors(recoil_plan* plan, void* cuda_stream, uint32_t* flags);
 
 /* Number of kernel launches the last recoil_plan_decode issued. */
 uint32_t recoil_plan_launches(const recoil_plan* plan);
+
+/* Warps per CTA the plan decodes with (the automatic choice when opts gave 0). */
+uint32_t recoil_plan_warps_per_cta(const recoil_plan* plan);
 
 void recoil_plan_free(recoil_plan* plan);
 

@@ -80,7 +80,7 @@ EXPORTS = [
     "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
     "recoil_pipeline_free", "recoil_shard", "recoil_encode_with_table",
     "recoil_serialized_size", "recoil_serialize", "recoil_deserialize", "recoil_encode_adaptive",
-    "recoil_plan_create_shard",
+    "recoil_plan_create_shard", "recoil_plan_warps_per_cta",
 ]
 
 _lib = None
@@ -115,6 +115,8 @@ def lib():
         L.recoil_plan_decode.argtypes = [vp, vp, vp]
         L.recoil_plan_errors.argtypes = [vp, vp, C.POINTER(u32)]
         L.recoil_plan_launches.argtypes = [vp]
+        L.recoil_plan_warps_per_cta.argtypes = [vp]
+        L.recoil_plan_warps_per_cta.restype = u32
         L.recoil_plan_launches.restype = u32
         L.recoil_plan_free.argtypes = [vp]
         L.recoil_plan_free.restype = None
@@ -382,9 +384,17 @@ class Plan:
     def launches(self) -> int:
         return int(lib().recoil_plan_launches(self.handle))
 
+    @property
+    def warps_per_cta(self) -> int:
+        return int(lib().recoil_plan_warps_per_cta(self.handle))
+
 
 def recoil_plan_create(streams, opts=None) -> Plan:
     return Plan(streams, opts)
+
+
+def recoil_plan_warps_per_cta(plan: Plan) -> int:
+    return plan.warps_per_cta
 
 
 def recoil_plan_create_shard(stream, world: int, rank: int, opts=None):
