@@ -87,20 +87,20 @@ struct Tables {
 // modulo 2^16 and exact since every f of an adaptive model is below 2^16.
 //
 // GUIDED (alphabets up to 256): the row's guide holds, for each of 2^g equal
-// buckets of slots, the symbol owning the bucket's first slot; the symbol of
-// `slot` lies between the guides of its bucket and of the next, and a binary
-// search narrows that range (usually empty: one lookup). Otherwise a 12-step
-// binary search over the whole row.
+// buckets of slots, the symbols owning the bucket's first slot (low byte) and
+// the next bucket's first slot (high byte); the symbol of `slot` lies between
+// the two, and a binary search narrows that range (usually empty: one
+// lookup). Otherwise a 12-step binary search over the whole row.
 template <bool GUIDED>
 struct AdaptiveTables {
   const uint16_t* cdf;
-  const uint8_t* guide;
+  const uint16_t* guide;
   uint32_t stride, gstride, gshift, A;
   __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream& st) {
     cdf = reinterpret_cast<const uint16_t*>(smem);
-    guide = smem + (size_t)st.n_tables * st.row_stride * 2;
+    guide = reinterpret_cast<const uint16_t*>(smem + (size_t)st.n_tables * st.row_stride * 2);
     stride = st.row_stride;
-    gstride = st.guide_stride;
+    gstride = st.guide_stride / 2;
     gshift = st.n_bits > kGuideBits ? st.n_bits - kGuideBits : 0;
     A = st.alphabet;
   }
@@ -109,10 +109,9 @@ struct AdaptiveTables {
     const uint16_t* row = cdf + t * stride;
     uint32_t s;
     if (GUIDED) {
-      const uint8_t* gd = guide + t * gstride;
-      const uint32_t b = slot >> gshift;
-      s = gd[b];
-      uint32_t hi = gd[b + 1];
+      const uint32_t pair = guide[t * gstride + (slot >> gshift)];
+      s = pair & 0xffu;
+      uint32_t hi = pair >> 8;
       while (s < hi) {                                  // bounded: hi - s halves
         const uint32_t mid = (s + hi + 1) >> 1;
         if (row[mid] < slot) s = mid; else hi = mid - 1;

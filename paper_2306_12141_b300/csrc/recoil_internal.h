@@ -107,7 +107,7 @@ struct alignas(16) DevStream {
   uint32_t slot_bytes;       // generic kinds: bytes of the slot -> symbol part (multiple of 16)
   uint32_t row_stride;       // adaptive: 16-bit entries between CDF rows (odd number of 32-bit words)
   uint32_t n_tables;         // adaptive: CDF rows
-  uint32_t guide_stride;     // guided adaptive kinds: bytes between guide rows (after all CDF rows)
+  uint32_t guide_stride;     // guided adaptive kinds: bytes between guide rows (after all CDF rows; 2 B per bucket)
 };
 static_assert(sizeof(DevStream) == 64, "DevStream layout");
 
