@@ -358,6 +358,9 @@ typedef struct {
   uint32_t flags;            /* RECOIL_SERVE_* */
   size_t meta_bytes;         /* descriptor area per launch (default 4 MiB) */
   double timeout_s;          /* wall-clock limit of the run (default 60 s) */
+  uint32_t max_split_symbols; /* longest split a request is combined to (default 131072): a
+                                 split is one warp's sequential work, so this bounds latency */
+  uint32_t reserved;
 } recoil_serve_opts;
 
 #define RECOIL_SERVE_PER_REQUEST 1u  /* baseline: one launch per request with every encoded split, one at a time */
@@ -393,7 +396,9 @@ int recoil_serve_arena_size(const recoil_stream* const* pool, uint32_t pool_coun
  * stream req_stream[r] at req_arrival_s[r] (seconds from the start, non-
  * decreasing) and is replayed in real time. Arrived requests are admitted in
  * order while the budget and a launch slot allow, combined to their share of
- * the free warp slots, and launched together as one persistent decode on the
+ * the free warp slots (but to at least n_syms / max_split_symbols splits, so
+ * that a large request admitted into a busy device is not left with a few
+ * long splits), and launched together as one persistent decode on the
  * slot's CUDA stream; launches overlap on the device. Outputs go to
  * d_req_outs[r] (caller device buffers of n_syms * sym_bytes) or, with
  * d_req_outs NULL, to arena memory that is reused once a request completes.

@@ -47,7 +47,7 @@ class BatchOpts(C.Structure):
 class ServeOpts(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("max_inflight", C.c_uint32), ("max_batch", C.c_uint32),
                 ("warps_per_cta", C.c_uint32), ("flags", C.c_uint32), ("meta_bytes", C.c_size_t),
-                ("timeout_s", C.c_double)]
+                ("timeout_s", C.c_double), ("max_split_symbols", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class RequestResult(C.Structure):
@@ -539,9 +539,9 @@ def recoil_pipeline_free(p: Pipeline) -> None:
 
 
 def _serve_opts(budget_bytes, max_inflight=0, max_batch=0, warps_per_cta=0, per_request=False, meta_bytes=0,
-                timeout_s=0.0):
+                timeout_s=0.0, max_split_symbols=0):
     return ServeOpts(int(budget_bytes), max_inflight, max_batch, warps_per_cta,
-                     SERVE_PER_REQUEST if per_request else 0, meta_bytes, timeout_s)
+                     SERVE_PER_REQUEST if per_request else 0, meta_bytes, timeout_s, max_split_symbols, 0)
 
 
 def recoil_serve_arena_size(pool, budget_bytes, **kw) -> int:

@@ -135,6 +135,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   const uint32_t max_batch = per_request ? 1 : (opts->max_batch ? opts->max_batch : 64);
   const size_t meta_cap = align_up(opts->meta_bytes ? opts->meta_bytes : (4u << 20), kAlign);
   const double timeout = opts->timeout_s > 0 ? opts->timeout_s : 60.0;
+  const uint64_t max_split = opts->max_split_symbols ? opts->max_split_symbols : 131072;
   if (!warps_supported(warps)) return fail(RECOIL_EINVAL, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
 
   // resident pool: words and tables of every pool stream, uploaded once
@@ -296,10 +297,13 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
           const recoil_stream* src = pool[req_stream[r]];
           uint32_t target = (uint32_t)src->entries.size() + 1;
           if (!per_request) {
+            // the request's share of the free warps, but splits no longer than
+            // max_split: a split is one warp's sequential work
             const double share = syms_batch ? (double)src->n_syms / (double)syms_batch : 1.0;
-            uint32_t want = (uint32_t)std::max(1.0, std::floor(free_w * share));
+            uint64_t want = (uint64_t)std::max(1.0, std::floor(free_w * share));
+            want = std::max<uint64_t>(want, (src->n_syms + max_split - 1) / max_split);
             want = (want + warps - 1) / warps * warps;
-            target = std::min(target, want);
+            target = (uint32_t)std::min<uint64_t>(target, want);
           }
           recoil_stream* c = nullptr;
           if (recoil_combine_splits(src, target, &c) != RECOIL_OK) {
