@@ -283,3 +283,21 @@ def test_gpu_adaptive_corrupt_words_flagged(recoil_lib):
     plan.decode([out.data_ptr()])
     assert plan.errors() == 0
     assert np.array_equal(out.cpu().numpy().view(np.uint16), s)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("N", [1, 31, 32, 33, 1023, 4097])
+def test_gpu_adaptive_edge_lengths(recoil_lib, N):
+    """Short adaptive streams (idle coders in the top group, a single group), alone and as a
+    batch of one-table streams (warp-queue launch)."""
+    R = recoil_lib
+    a, tables, s, tid = _case(N, 300 + N)
+    p = R.encode_adaptive(s, 16, tables, tid, 4)
+    (out,) = _gpu_decode(R, [p], {"warps_per_cta": 4})
+    assert np.array_equal(out, s)
+    o = oracle.encode_adaptive_with_splits(s, tid, tables, 16, 4)
+    assert np.array_equal(out, oracle.decode_splits(o).astype(np.uint16))
+    many = [R.encode_adaptive(s[: max(1, N - k)], 16, tables, tid[: max(1, N - k)], 4) for k in range(6)]
+    outs = _gpu_decode(R, many, {"warps_per_cta": 8})
+    for k, o2 in enumerate(outs):
+        assert np.array_equal(o2, s[: max(1, N - k)]), k
