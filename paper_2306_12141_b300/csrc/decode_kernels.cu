@@ -364,7 +364,7 @@ struct EntryDecoder {
 // blocks to keep RECOIL_RESIDENT_WARPS warps per SM, which caps registers at
 // 65536 / (32 * RECOIL_RESIDENT_WARPS) a thread.
 #ifndef RECOIL_RESIDENT_WARPS
-#define RECOIL_RESIDENT_WARPS 48
+#define RECOIL_RESIDENT_WARPS 56
 #endif
 // The adaptive step needs more registers (the CDF search): 32 warps per SM.
 #ifndef RECOIL_RESIDENT_WARPS_ADAPTIVE
