@@ -449,6 +449,14 @@ def run_adaptive(a):
             sweep[str(k)] = round(out_bytes / (statistics.mean(t) * 1e-3) / 1e9, 1)
             del sws
         c = R.combine_splits(enc, a.splits)
+        tuned = None
+        if not warps:
+            # the autotuner picks the CTA size for the workload's split count (untimed)
+            tws = torch.empty(R.autotune_workspace_size([c]), dtype=torch.uint8, device=dev)
+            best, tms = R.autotune([c], [out.data_ptr()], tws, tws.numel(), cs, steps=3, keep_splits=True)
+            warps = best["warps_per_cta"]
+            tuned = {"warps_per_cta": warps, "ms": round(tms, 4)}
+            del tws
         plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
         warps = plan.warps_per_cta
         ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
@@ -491,7 +499,8 @@ def run_adaptive(a):
             "config": {"workload": "adaptive: 2^27 uint16 latents, symbol i = clip(rint(128 + sigma_t Z)) with "
                                    "t_i ~ clip(rint(N(20, 12)), 0, 63), 64 log-spaced Gaussian scale tables "
                                    "(0.11..256) over 256 values, n=16, W=32",
-                       "splits": c.info["n_entries"], "warps_per_cta": warps, "symbols_bytes": out_bytes,
+                       "splits": c.info["n_entries"], "warps_per_cta": warps, "autotuned": tuned,
+                       "symbols_bytes": out_bytes,
                        "compressed_bytes": 2 * c.info["n_words"] + 4 * 32, "table_number_bytes": len(s),
                        "l2": "inputs larger than L2 (no flush)", "scale": a.scale},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -540,6 +549,15 @@ def run_ours(a):
         tuned = {"warps_per_cta": best["warps_per_cta"], "split_symbols": best["split_symbols"],
                  "ms": round(tms, 4)}
         split_symbols, warps = best["split_symbols"], best["warps_per_cta"]
+        del tws
+    elif not batch and a.warps == 0:
+        # the split count is the workload's; the autotuner picks the CTA size for it (untimed)
+        tws = torch.empty(R.autotune_workspace_size(streams), dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(cs):
+            best, tms = R.autotune(streams, out_ptrs, tws, tws.numel(), cs, steps=3, keep_splits=True)
+        tuned = {"warps_per_cta": best["warps_per_cta"], "split_symbols": 0, "ms": round(tms, 4),
+                 "candidates": "warps per CTA 4, 8, 16 at the workload's split count"}
+        split_symbols, warps = 0, best["warps_per_cta"]
         del tws
     else:
         split_symbols = (65536 if a.split_symbols < 0 else a.split_symbols) if batch else 0

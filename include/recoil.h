@@ -421,6 +421,7 @@ typedef struct {
 } recoil_tune_opts;
 
 #define RECOIL_TUNE_REFRESH 1u     /* ignore a cached result and tune again */
+#define RECOIL_TUNE_KEEP_SPLITS 2u /* keep the streams' split counts; tune warps_per_cta only */
 
 /* Workspace bytes recoil_autotune needs for these streams (the largest candidate). */
 int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t count, size_t* bytes);
@@ -429,7 +430,9 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
  * Choose batch options for these streams by measurement (the batching pattern
  * of the paper's decoder-adaptive parallelism, Sec. 3.3: the decoder picks the
  * split count that suits it). Candidates: warps_per_cta in {4, 8, 16} times
- * split_symbols in {32 Ki, 64 Ki, 128 Ki, 256 Ki}. Each candidate decodes the
+ * split_symbols in {32 Ki, 64 Ki, 128 Ki, 256 Ki} (with RECOIL_TUNE_KEEP_SPLITS:
+ * warps_per_cta in {4, 8, 16} on the streams as given, split_symbols 0, for a
+ * decoder whose split count is already chosen). Each candidate decodes the
  * streams into d_outs (caller-owned, as for recoil_plan_decode) once untimed
  * and `steps` times timed with CUDA events on cuda_stream; the lowest median
  * wins and is written to *best (ctas_per_sm = 0, flags = 0) with its time in

@@ -69,6 +69,7 @@ class TuneOpts(C.Structure):
 
 
 TUNE_REFRESH = 1
+TUNE_KEEP_SPLITS = 2
 
 EXPORTS = [
     "recoil_encode_with_splits", "recoil_combine_splits", "recoil_stream_info", "recoil_stream_export",
@@ -471,9 +472,12 @@ def recoil_autotune_workspace_size(streams) -> int:
 
 
 def recoil_autotune(streams, outs, workspace, nbytes: int, cuda_stream=None, steps: int = 3,
-                    cache_path: str | None = None, refresh: bool = False) -> tuple[dict, float]:
-    """Measured best batch options for these streams: ({warps_per_cta, split_symbols, ...}, ms)."""
-    t = TuneOpts(steps, TUNE_REFRESH if refresh else 0, cache_path.encode() if cache_path else None)
+                    cache_path: str | None = None, refresh: bool = False,
+                    keep_splits: bool = False) -> tuple[dict, float]:
+    """Measured best batch options for these streams: ({warps_per_cta, split_symbols, ...}, ms).
+    keep_splits: tune warps_per_cta only, on the streams' own split counts."""
+    flags = (TUNE_REFRESH if refresh else 0) | (TUNE_KEEP_SPLITS if keep_splits else 0)
+    t = TuneOpts(steps, flags, cache_path.encode() if cache_path else None)
     best = BatchOpts()
     ms = C.c_float()
     _check(lib().recoil_autotune(_handles(streams), len(streams), _ptr_array(outs), _ptr(workspace), nbytes,

@@ -23,6 +23,19 @@ namespace {
 const uint32_t kWarps[] = {4, 8, 16};
 const uint32_t kSplit[] = {32768, 65536, 131072, 262144};
 
+// Candidate options: warps x split sizes, or warps alone on the streams' own splits.
+std::vector<recoil_batch_opts> candidates(bool keep_splits) {
+  std::vector<recoil_batch_opts> c;
+  for (uint32_t w : kWarps) {
+    if (keep_splits) {
+      c.push_back(recoil_batch_opts{w, 0, 0, 0});
+      continue;
+    }
+    for (uint32_t sp : kSplit) c.push_back(recoil_batch_opts{w, 0, sp, 0});
+  }
+  return c;
+}
+
 std::string tune_key(const recoil_stream* const* s, uint32_t count) {
   int dev = 0, sms = 0;
   cudaDeviceProp prop;
@@ -87,9 +100,8 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
   clear_error();
   if (!bytes) return fail(RECOIL_EINVAL, "null argument");
   size_t mx = 0;
-  for (uint32_t w : kWarps)
-    for (uint32_t sp : kSplit) {
-      recoil_batch_opts o{w, 0, sp, 0};
+  for (bool keep : {false, true})
+    for (recoil_batch_opts o : candidates(keep)) {
       size_t b = 0;
       int rc = recoil_workspace_size(streams, count, &o, &b);
       if (rc) return rc;
@@ -107,7 +119,8 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
   const uint32_t steps = topts && topts->steps ? topts->steps : 3;
   const char* cache = topts ? topts->cache_path : nullptr;
   const bool refresh = topts && (topts->flags & RECOIL_TUNE_REFRESH);
-  const std::string key = tune_key(streams, count);
+  const bool keep = topts && (topts->flags & RECOIL_TUNE_KEEP_SPLITS);
+  const std::string key = tune_key(streams, count) + (keep ? "|keep" : "");
   float ms = 0;
   recoil_batch_opts hit{};
   if (!refresh && cache_lookup(cache, key, &hit, &ms)) {
@@ -121,30 +134,29 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
     for (Candidate& c : cands) recoil_plan_free(c.plan);
   };
   size_t bulk = 0;
-  for (uint32_t w : kWarps)
-    for (uint32_t sp : kSplit) {
-      Candidate c;
-      c.opts = recoil_batch_opts{w, 0, sp, 0};
-      int rc = recoil_plan_create(streams, count, &c.opts, &c.plan);
-      if (rc) {
-        cleanup();
-        return rc;
-      }
-      size_t need = 0;
-      recoil_plan_workspace_size(c.plan, &need);
-      if (need > ws_bytes) {
-        recoil_plan_free(c.plan);
-        cleanup();
-        return fail(RECOIL_ENOMEM, "workspace too small for tuning (see recoil_autotune_workspace_size)");
-      }
-      if (cands.empty()) bulk = plan_bulk_bytes(c.plan);
-      if (plan_bulk_bytes(c.plan) != bulk) {
-        recoil_plan_free(c.plan);
-        cleanup();
-        return fail(RECOIL_EINVAL, "internal: candidates disagree on the bulk layout");
-      }
-      cands.push_back(c);
+  for (const recoil_batch_opts& o : candidates(keep)) {
+    Candidate c;
+    c.opts = o;
+    int rc = recoil_plan_create(streams, count, &c.opts, &c.plan);
+    if (rc) {
+      cleanup();
+      return rc;
     }
+    size_t need = 0;
+    recoil_plan_workspace_size(c.plan, &need);
+    if (need > ws_bytes) {
+      recoil_plan_free(c.plan);
+      cleanup();
+      return fail(RECOIL_ENOMEM, "workspace too small for tuning (see recoil_autotune_workspace_size)");
+    }
+    if (cands.empty()) bulk = plan_bulk_bytes(c.plan);
+    if (plan_bulk_bytes(c.plan) != bulk) {
+      recoil_plan_free(c.plan);
+      cleanup();
+      return fail(RECOIL_EINVAL, "internal: candidates disagree on the bulk layout");
+    }
+    cands.push_back(c);
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);

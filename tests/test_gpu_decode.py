@@ -263,6 +263,11 @@ def test_autotune_chooses_a_working_configuration(recoil_lib, tmp_path):
     res = gpu_decode(R, streams, best)
     for s, out in zip(syms, res):
         assert np.array_equal(out, s)
+    # CTA size only, on the streams' own split counts (cached under its own key)
+    keep, ms3 = R.autotune(streams, ptrs, ws, need, cs, steps=2, cache_path=cache, keep_splits=True)
+    assert keep["warps_per_cta"] in (4, 8, 16) and keep["split_symbols"] == 0 and ms3 > 0
+    for s, out in zip(syms, gpu_decode(R, streams, keep)):
+        assert np.array_equal(out, s)
 
 
 def test_pipeline_decodes_host_to_host(recoil_lib):
