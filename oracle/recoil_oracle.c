@@ -24,6 +24,12 @@
  *   - adaptive coding ............. Sec. 3.1 (the PDF of every coding step is chosen
  *                                   by the symbol index; here one row of a table set)
  *
+ * Parity unpinned against the paper: the quantiser's and the heuristic's exact
+ * outputs (the paper gives neither procedure in enough detail to reproduce its
+ * numbers); they are pinned by hand cases, invariants and the exhaustive
+ * argmin of Eq. 7 instead. Every other function is pinned to the paper or to
+ * the mathematics by the oracle tests.
+ *
  * Readings where the paper is silent (all listed in the design notes):
  *   - Quantiser: f[s] = max(1, round_half_even(c[s] 2^n / N)) for present
  *     symbols, 0 otherwise, then +-1 corrections until the sum is 2^n, visiting
