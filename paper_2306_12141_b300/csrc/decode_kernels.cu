@@ -16,18 +16,22 @@
 //
 // Memory: decoder tables are staged in shared memory once per work item
 // (Sec. 4.4 packs symbol, f and F into one 32-bit entry for 8-bit symbols and
-// n <= 12); the compressed words a warp is about to consume sit in a per-warp
-// shared ring refilled 512 bytes at a time with one 16-byte load per lane,
-// issued a chunk ahead so that the dependent renormalisation reads never wait
-// on HBM. Symbol stores are one coalesced 32-byte (or 64-byte) warp store per
-// group step.
+// n <= 12; adaptive models stage one CDF row per PDF, Sec. 3.1); the
+// compressed words a warp is about to consume sit in a per-warp shared ring
+// refilled 512 bytes at a time with one 16-byte load per lane, issued a chunk
+// ahead so that the dependent renormalisation reads never wait on HBM.
+// Symbol stores are one coalesced 32-byte (or 64-byte) warp store per group
+// step.
 //
 // Scheduling: persistent CTAs pop work items (up to `warps` entries of one
-// stream) from a device counter; a CTA restages tables only when the stream
-// changes. Every loop is bounded by the entry's group range, every word read
-// comes from the shared ring (in bounds by construction) and every global
-// load of a chunk is guarded by the chunk index, so a corrupt stream yields an
-// error flag, never a fault or a hang.
+// stream) from a device counter and their warps take the item's entries from
+// a shared counter; a CTA restages tables only when the stream changes. When
+// one table serves the whole launch, every entry is an item of its own and
+// each warp pops items alone (no CTA barrier between splits). Every loop is
+// bounded by the entry's group range, every word read comes from the shared
+// ring (in bounds by construction) and every global load of a chunk is
+// guarded by the chunk index, so a corrupt stream yields an error flag, never
+// a fault or a hang.
 #include <cuda_runtime.h>
 
 #include "recoil_internal.h"
