@@ -94,3 +94,25 @@ def test_timeout_is_reported_not_hung(recoil_lib):
     with pytest.raises(R.RecoilError) as e:
         R.serve(pool, picks, arrive, arena, need, 16 << 20, timeout_s=0.3)
     assert e.value.code == R.ETIMEOUT
+
+
+def test_admission_bounds_split_length(recoil_lib):
+    """Every request is combined to at least n_syms / max_split_symbols splits (rounded to
+    whole CTAs, capped by its encoded entries), however busy the device is."""
+    R = recoil_lib
+    syms, pool = _pool(R, count=12, seed=55)
+    n_req = 300
+    picks = workloads.request_picks(len(pool), n_req, seed=56)
+    arrive = workloads.poisson_arrivals(50_000.0, n_req, seed=56)
+    budget = 256 << 20
+    need = R.serve_arena_size(pool, budget)
+    arena = torch.empty(need, dtype=torch.uint8, device="cuda")
+    max_split, warps = 8192, 8
+    res, stats = R.serve(pool, picks, arrive, arena, need, budget, warps_per_cta=warps, max_inflight=4,
+                         max_split_symbols=max_split, timeout_s=60.0)
+    assert stats["requests"] == n_req
+    for r, p in enumerate(picks):
+        n, enc = pool[p].info["n_syms"], pool[p].info["n_entries"]
+        floor = -(-n // max_split)
+        floor = -(-floor // warps) * warps
+        assert res["splits"][r] >= min(enc, floor), (r, res["splits"][r], enc, floor)
