@@ -316,7 +316,9 @@ typedef struct recoil_pipeline recoil_pipeline;   /* opaque: grouped plans + cop
 /*
  * Prepare host-to-host decoding of `count` streams with copy/compute overlap:
  * the streams are cut into `groups` (0 = 8) groups of about equal output
- * bytes, each with its own plan (opts as for recoil_plan_create), a page-
+ * bytes -- a stream larger than that share is cut into runs of its splits
+ * (recoil_plan_create_shard), so even one stream overlaps copies and
+ * decoding -- each with its own plan (opts as for recoil_plan_create), a page-
  * locked copy of its descriptors and a page-locked image of its words, table
  * numbers and tables as they lie in the workspace (so a group is copied in
  * with two copies; the pipeline holds about the streams' compressed size in

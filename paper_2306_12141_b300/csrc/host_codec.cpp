@@ -288,8 +288,15 @@ static int encode_common(const void* syms, uint64_t n_syms, const recoil_params*
     std::vector<uint64_t> qs;
     place_splits(rec, n_syms, max_splits, qs);
     s->entries.resize(qs.size());
-    for (size_t k = 0; k < qs.size(); k++)
-      if (!entry_at(rec, qs[k], s->entries[k])) return fail(RECOIL_ECORRUPT, "internal: split word not usable");
+    for (size_t k = 0; k < qs.size(); k++) {
+      Entry& e = s->entries[k];
+      if (!entry_at(rec, qs[k], e)) return fail(RECOIL_ECORRUPT, "internal: split word not usable");
+      // the decoder reads word p right after decoding symbol rec.sym[p] (Eq. 4
+      // mirrors Eq. 3), so the thread that stops at symbol m reads no word
+      // below the first one recorded for a symbol >= m
+      const uint32_t m = *std::min_element(e.idx, e.idx + kW);
+      e.wlo = (uint64_t)(std::lower_bound(rec.sym.begin(), rec.sym.end(), m) - rec.sym.begin());
+    }
     s->words = words;
     *out = s.release();
     return RECOIL_OK;

@@ -37,6 +37,8 @@ struct Group {
   size_t ws_off = 0, ws_bytes = 0;
   size_t stage_off = 0, stage_bytes = 0;
   std::vector<size_t> out_off;       // per member, inside the group's staging
+  std::vector<size_t> out_len;       // per member: bytes decoded (a run: its symbol range)
+  std::vector<size_t> host_off;      // per member: where they go in the caller's buffer
   uint8_t* meta = nullptr;           // page-locked copies of the plan's descriptors and tables
   size_t meta_bytes = 0, off_meta = 0, off_outs = 0;
   uint8_t* bulk = nullptr;           // page-locked image of the bulk region (words, table numbers, tables)
@@ -51,6 +53,7 @@ struct Group {
 
 struct recoil_pipeline {
   std::vector<Group> groups;
+  std::vector<std::unique_ptr<recoil_stream>> owned;   // streams combined before being cut into runs
   std::vector<size_t> out_bytes;
   size_t ws_bytes = 0, stage_bytes = 0;
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
@@ -81,7 +84,6 @@ int recoil_pipeline_create(const recoil_stream* const* streams, uint32_t count, 
   if (!out || (count && !streams)) return fail(RECOIL_EINVAL, "null argument");
   *out = nullptr;
   if (groups < 1) groups = 8;
-  groups = std::max<uint32_t>(1, std::min<uint32_t>(groups, count ? count : 1));
   try {
     std::unique_ptr<recoil_pipeline> P(new recoil_pipeline());
     P->out_bytes.resize(count);
@@ -91,31 +93,73 @@ int recoil_pipeline_create(const recoil_stream* const* streams, uint32_t count, 
       P->out_bytes[i] = streams[i]->n_syms * streams[i]->sym_bytes;
       total += P->out_bytes[i];
     }
-    // contiguous groups of about total / groups output bytes
-    P->groups.resize(groups);
+    // Streams of more than total / groups output bytes are cut into runs of
+    // splits (shard plans: each run decodes a contiguous symbol range and
+    // stages only the words it reads), one group per run; the other streams
+    // form contiguous groups of about total / groups output bytes.
+    const uint64_t share = std::max<uint64_t>(1, (total + groups - 1) / groups);
+    recoil_batch_opts run_opts{};
+    if (opts) run_opts = *opts;
+    run_opts.split_symbols = 0;
     uint64_t acc = 0;
-    uint32_t g = 0;
-    for (uint32_t i = 0; i < count; i++) {
-      P->groups[g].members.push_back(i);
-      acc += P->out_bytes[i];
-      if (g + 1 < groups && acc >= (total * (g + 1) + groups - 1) / groups) g++;
-    }
-    P->groups.erase(std::remove_if(P->groups.begin(), P->groups.end(), [](const Group& x) { return x.members.empty(); }),
-                    P->groups.end());
+    bool open = false;
     cudaError_t e = cudaSuccess;
+    for (uint32_t i = 0; i < count; i++) {
+      const recoil_stream* s = streams[i];
+      const uint64_t runs = P->out_bytes[i] / share;
+      if (runs < 2) {
+        if (!open) {
+          P->groups.emplace_back();
+          open = true;
+          acc = 0;
+        }
+        Group& G = P->groups.back();
+        G.members.push_back(i);
+        G.out_len.push_back(P->out_bytes[i]);
+        G.host_off.push_back(0);
+        acc += P->out_bytes[i];
+        if (acc >= share) open = false;
+        continue;
+      }
+      open = false;
+      const recoil_stream* src = s;
+      if (opts && opts->split_symbols) {
+        // the split size the caller asked for, rounded to whole CTAs, before cutting into runs
+        const uint32_t w = opts->warps_per_cta ? opts->warps_per_cta : 8;
+        uint64_t want = std::max<uint64_t>(1, (s->n_syms + opts->split_symbols - 1) / opts->split_symbols);
+        want = (want + w - 1) / w * w;
+        recoil_stream* c = nullptr;
+        int rc = recoil_combine_splits(s, (uint32_t)std::min<uint64_t>(want, 0xffffffffu), &c);
+        if (rc) return rc;
+        P->owned.emplace_back(c);
+        src = c;
+      }
+      for (uint64_t r = 0; r < runs; r++) {
+        Group G;
+        uint64_t lo = 0, hi = 0;
+        int rc = recoil_plan_create_shard(src, (uint32_t)runs, (uint32_t)r, &run_opts, &G.plan, &lo, &hi);
+        if (rc) return rc;
+        G.members.push_back(i);
+        G.out_len.push_back((hi - lo) * s->sym_bytes);
+        G.host_off.push_back(lo * s->sym_bytes);
+        P->groups.push_back(std::move(G));
+      }
+    }
     for (Group& G : P->groups) {
-      std::vector<const recoil_stream*> sub;
-      for (uint32_t i : G.members) sub.push_back(streams[i]);
-      int rc = recoil_plan_create(sub.data(), (uint32_t)sub.size(), opts, &G.plan);
-      if (rc) return rc;
+      if (!G.plan) {
+        std::vector<const recoil_stream*> sub;
+        for (uint32_t i : G.members) sub.push_back(streams[i]);
+        int rc = recoil_plan_create(sub.data(), (uint32_t)sub.size(), opts, &G.plan);
+        if (rc) return rc;
+      }
       recoil_plan_workspace_size(G.plan, &G.ws_bytes);
       G.ws_off = P->ws_bytes;
       P->ws_bytes += align_up(G.ws_bytes, kAlign);
       G.stage_off = P->stage_bytes;
-      for (uint32_t i : G.members) {                 // back to back, each on its element size
-        G.stage_bytes = align_up(G.stage_bytes, streams[i]->sym_bytes);
+      for (size_t k = 0; k < G.members.size(); k++) {   // back to back, each on its element size
+        G.stage_bytes = align_up(G.stage_bytes, streams[G.members[k]]->sym_bytes);
         G.out_off.push_back(G.stage_bytes);
-        G.stage_bytes += P->out_bytes[i];
+        G.stage_bytes += G.out_len[k];
       }
       G.stage_bytes = align_up(std::max<size_t>(1, G.stage_bytes), kAlign);
       P->stage_bytes += G.stage_bytes;
@@ -172,10 +216,13 @@ int recoil_pipeline_run(recoil_pipeline* P, void* const* h_outs, void* d_ws, siz
     std::vector<void*> outs(G.members.size());
     for (size_t k = 0; k < G.members.size(); k++) outs[k] = stage + G.stage_off + G.out_off[k];
     if (G.bound_stage != stage) {
-      // the descriptor copy carries the output pointers: write them once the
-      // previous copy-in from this page-locked buffer has finished
+      // the descriptor copy carries the output pointers, as the kernels index
+      // them (a run's are shifted back to its first symbol): write them once
+      // the previous copy-in from this page-locked buffer has finished
       if (G.used && (e = cudaEventSynchronize(G.in)) != cudaSuccess) break;
-      std::memcpy(G.meta + G.off_outs, outs.data(), outs.size() * sizeof(void*));
+      std::vector<void*> dev(outs.size());
+      plan_kernel_outs(G.plan, outs.data(), dev.data());
+      std::memcpy(G.meta + G.off_outs, dev.data(), dev.size() * sizeof(void*));
     }
     // copy-in, once the previous run's decode of this group is done with the region
     if (G.used) e = cudaStreamWaitEvent(P->s_in, G.dec, 0);
@@ -204,15 +251,14 @@ int recoil_pipeline_run(recoil_pipeline* P, void* const* h_outs, void* d_ws, siz
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_out, G.dec, 0);
     for (size_t k = 0; k < G.members.size() && e == cudaSuccess;) {
       // one copy for each run of members that follow each other on both sides
-      const uint32_t i = G.members[k];
-      size_t bytes = P->out_bytes[i], j = k + 1;
+      uint8_t* dst = (uint8_t*)h_outs[G.members[k]] + G.host_off[k];
+      size_t bytes = G.out_len[k], j = k + 1;
       while (j < G.members.size()) {
-        const uint32_t n = G.members[j];
-        if ((uint8_t*)h_outs[n] != (uint8_t*)h_outs[i] + bytes || G.out_off[j] != G.out_off[k] + bytes) break;
-        bytes += P->out_bytes[n];
+        if ((uint8_t*)h_outs[G.members[j]] + G.host_off[j] != dst + bytes || G.out_off[j] != G.out_off[k] + bytes) break;
+        bytes += G.out_len[j];
         j++;
       }
-      if (bytes) e = cudaMemcpyAsync(h_outs[i], outs[k], bytes, cudaMemcpyDeviceToHost, P->s_out);
+      if (bytes) e = cudaMemcpyAsync(dst, outs[k], bytes, cudaMemcpyDeviceToHost, P->s_out);
       k = j;
     }
     if (e == cudaSuccess) e = cudaEventRecord(G.out, P->s_out);

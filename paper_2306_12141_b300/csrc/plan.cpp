@@ -116,7 +116,7 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
 }  // namespace
 
 // Device entries of a stream: kept regular entries in order, then the final one.
-void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>& out) {
+void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>& out, uint64_t word_base) {
   const uint32_t N = (uint32_t)s.n_syms;
   uint32_t prev_m = 0;
   for (const Entry& e : s.entries) {
@@ -130,7 +130,7 @@ void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>
       mn = std::min(mn, e.idx[j]);
       mx = std::max(mx, e.idx[j]);
     }
-    d.q = (int32_t)e.word;
+    d.q = (int32_t)((int64_t)e.word - (int64_t)word_base);
     d.g_top = (int32_t)(mx / kW) + 1;
     d.lo = prev_m;
     d.hi1 = mn;                                      // owns [previous m, m - 1] (Sec. 4.1.3)
@@ -151,7 +151,7 @@ void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>
     }
     top = std::max(top, d.act[j]);
   }
-  d.q = (int32_t)s.n_words() - 1;
+  d.q = (int32_t)((int64_t)s.n_words() - 1 - (int64_t)word_base);
   d.g_top = top;
   d.lo = prev_m;
   d.hi1 = N;
@@ -172,7 +172,8 @@ struct recoil_plan {
   std::vector<uint8_t> tables;
   size_t off_outs = 0, off_streams = 0, off_items = 0, off_entries = 0;
   size_t off_tables = 0, off_meta = 0, ws_bytes = 0;   // words start at 0
-  std::vector<uint64_t> word_off;                      // per stream, in words
+  std::vector<uint64_t> word_off;                      // per stream: its staged words' place in the pool, in words
+  std::vector<uint64_t> word_lo, word_cnt;             // per stream: first staged word and how many are staged
   std::vector<uint64_t> tid_off;                       // per adaptive stream: its table numbers, in words
   uint32_t n_items = 0;
   uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {}, kind_warp_queue[kKinds] = {};
@@ -216,6 +217,8 @@ static int plan_build(recoil_plan* P) {
   size_t table_off = 0;
   uint64_t word_off = 0;
   P->word_off.resize(count);
+  P->word_lo.assign(count, 0);
+  P->word_cnt.assign(count, 0);
   P->tid_off.assign(count, 0);
   P->stream_kind.resize(count);
   std::vector<std::pair<size_t, const std::vector<uint8_t>*>> tabs;
@@ -234,11 +237,28 @@ static int plan_build(recoil_plan* P) {
     d.sym_bytes = s.sym_bytes;
     d.table_bytes = (uint32_t)img.size();
     d.slot_bytes = slot_bytes;
+    // staged words: all of them, or for a shard plan the window its run reads,
+    // from the lowest word of the thread that stops at the run's low end
+    // (recorded at encoding) to the highest split word of the run, in chunks
+    uint64_t wlo = 0, whi = s.n_words();
+    if (P->shard) {
+      const uint32_t K = (uint32_t)s.entries.size() + 1;
+      if (P->entry_first >= P->entry_last) {
+        whi = 0;
+      } else {
+        if (P->entry_first > 0) wlo = s.entries[P->entry_first - 1].wlo / kChunkWords * kChunkWords;
+        if (P->entry_last < K)
+          whi = std::min<uint64_t>(s.n_words(), (s.entries[P->entry_last - 1].word / kChunkWords + 1) * kChunkWords);
+        if (whi < wlo) whi = wlo;
+      }
+    }
     P->word_off[i] = word_off;
+    P->word_lo[i] = wlo;
+    P->word_cnt[i] = whi - wlo;
     P->stream_kind[i] = kind;
     tabs.push_back({table_off, &img});
     table_off += img.size();
-    word_off += align_up(s.n_words(), kChunkWords);
+    word_off += align_up(whi - wlo, kChunkWords);
     if (s.adaptive()) {
       // the table numbers follow the words, one byte per symbol, on a chunk boundary
       d.tid = word_off;
@@ -253,7 +273,7 @@ static int plan_build(recoil_plan* P) {
       return fail(RECOIL_EINVAL, "adaptive streams decode with 4, 8 or 16 warps per CTA");
 
     const size_t first = entries.size();
-    build_entries(s, i, entries);
+    build_entries(s, i, entries, wlo);
     size_t end_e = entries.size();
     if (P->shard) {
       end_e = first + P->entry_last;
@@ -414,8 +434,9 @@ namespace recoil {
 cudaError_t plan_upload_stream(const recoil_plan* P, size_t i, uint8_t* ws, cudaStream_t cs) {
   const Stream& s = *P->streams[i];
   cudaError_t e = cudaSuccess;
-  if (s.n_words())
-    e = cudaMemcpyAsync(ws + P->word_off[i] * 2, s.word_data(), s.n_words() * 2, cudaMemcpyHostToDevice, cs);
+  if (P->word_cnt[i])
+    e = cudaMemcpyAsync(ws + P->word_off[i] * 2, s.word_data() + P->word_lo[i], P->word_cnt[i] * 2,
+                        cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess && s.adaptive() && s.n_syms)
     e = cudaMemcpyAsync(ws + P->tid_off[i] * 2, s.tid->data(), s.n_syms, cudaMemcpyHostToDevice, cs);
   return e;
@@ -423,11 +444,18 @@ cudaError_t plan_upload_stream(const recoil_plan* P, size_t i, uint8_t* ws, cuda
 
 size_t plan_bulk_bytes(const recoil_plan* P) { return P->off_meta; }
 
+void plan_kernel_outs(const recoil_plan* P, void* const* outs, void** dev) {
+  const size_t count = P->streams.size();
+  for (size_t i = 0; i < count; i++) dev[i] = outs[i];
+  if (P->shard && count == 1 && dev[0])            // the buffer starts at the first owned symbol
+    dev[0] = (void*)((uintptr_t)dev[0] - P->out_shift * P->streams[0]->sym_bytes);
+}
+
 void plan_bulk_image(const recoil_plan* P, uint8_t* dst) {
   std::memset(dst, 0, P->off_meta);
   for (size_t i = 0; i < P->streams.size(); i++) {
     const Stream& s = *P->streams[i];
-    if (s.n_words()) std::memcpy(dst + P->word_off[i] * 2, s.word_data(), s.n_words() * 2);
+    if (P->word_cnt[i]) std::memcpy(dst + P->word_off[i] * 2, s.word_data() + P->word_lo[i], P->word_cnt[i] * 2);
     if (s.adaptive() && s.n_syms) std::memcpy(dst + P->tid_off[i] * 2, s.tid->data(), s.n_syms);
   }
   if (!P->tables.empty()) std::memcpy(dst + P->off_tables, P->tables.data(), P->tables.size());
@@ -587,9 +615,8 @@ int recoil_plan_decode(recoil_plan* P, void* const* d_outs, void* stream) {
       if (!d_outs[i] && P->streams[i]->n_syms && !(P->shard && P->n_items == 0))
         return fail(RECOIL_EINVAL, "null output buffer");
     P->outs.assign(d_outs, d_outs + count);
-    P->outs_dev = P->outs;
-    if (P->shard && count == 1 && P->outs_dev[0])  // the buffer starts at the first owned symbol
-      P->outs_dev[0] = (void*)((uintptr_t)P->outs_dev[0] - P->out_shift * P->streams[0]->sym_bytes);
+    P->outs_dev.resize(count);
+    plan_kernel_outs(P, d_outs, P->outs_dev.data());
     cudaError_t e = cudaMemcpyAsync(P->d_ws + P->off_meta + P->off_outs, P->outs_dev.data(), count * 8,
                                     cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "output pointer upload");

@@ -51,6 +51,8 @@ struct Entry {
   uint64_t word;             // split word q: the decoder's first read
   uint32_t idx[kW];          // recorded symbol index per coder (last symbol coded before the renorm)
   uint16_t y[kW];            // state right after that renormalisation (< L by Lemma 3.1)
+  uint64_t wlo = 0;          // lowest word read by the thread that stops at this entry's smallest
+                             // index (the first word written for a symbol at or above it); 0 if unknown
 };
 
 // Host stream: everything the encoder produced. Words are shared between a
@@ -184,7 +186,8 @@ struct recoil_plan;
 namespace recoil {
 void plan_image(const recoil_plan* plan, PlanImage* out);
 // Device entries of a stream's kept splits, the final-state entry last (plan.cpp).
-void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>& out);
+// word_base: the first word staged in the workspace (entries' q count from it).
+void build_entries(const Stream& s, uint32_t stream_index, std::vector<DevEntry>& out, uint64_t word_base = 0);
 // Upload the bulk region (words, tables) and/or the descriptors of a plan.
 int plan_upload_parts(recoil_plan* plan, void* d_ws, size_t ws_bytes, cudaStream_t s, bool bulk, bool meta);
 // Bytes of the bulk region at the start of a plan's workspace.
@@ -193,6 +196,10 @@ size_t plan_bulk_bytes(const recoil_plan* plan);
 const std::vector<const Stream*>& plan_streams(const recoil_plan* plan);
 // Copy stream k's bulk data (words; table numbers of an adaptive stream) to its place in ws.
 cudaError_t plan_upload_stream(const recoil_plan* plan, size_t k, uint8_t* ws, cudaStream_t s);
+// Output pointers as the kernels index them (symbol i of stream k at dev[k] +
+// i * sym_bytes): the caller's pointers, shifted back by the first owned
+// symbol for a shard plan, whose buffer starts there.
+void plan_kernel_outs(const recoil_plan* plan, void* const* outs, void** dev);
 // Host image of the bulk region (words, table numbers, tables) exactly as it
 // sits at the start of the workspace: plan_bulk_bytes bytes written to dst.
 void plan_bulk_image(const recoil_plan* plan, uint8_t* dst);

@@ -370,3 +370,31 @@ def test_shard_plans_adaptive_stream(recoil_lib):
         assert plan.errors() == 0
         pieces.append(buf.cpu().numpy()[: 2 * (hi - lo)].view(np.uint16))
     assert np.array_equal(np.concatenate(pieces), s)
+
+
+@pytest.mark.parametrize("groups", [1, 3, 8])
+def test_pipeline_cuts_a_large_stream_into_runs(recoil_lib, groups):
+    """One large stream (and a small one beside it) host to host: the large one is cut into
+    runs of splits that stage only their word windows, decode and copy out in turn."""
+    R = recoil_lib
+    big = workloads.Stream("z", 3_000_017, 1, 12, "zipf", {"s": 1.2}, seed=95).symbols()
+    small = workloads.Stream("l", 20_011, 1, 11, "laplace", {"mean": 128.0, "scale": 5.0}, seed=96).symbols()
+    a = workloads.AdaptiveStream("t", 1_000_003, seed=97)
+    tables = a.tables()
+    sa, tid = a.draw()
+    streams = [R.encode_with_splits(big, 12, 512), R.encode_with_splits(small, 11, 4),
+               R.encode_adaptive(sa, 16, tables, tid, 256)]
+    want = [big, small, sa]
+    pipe = R.Pipeline(streams, {"warps_per_cta": 8}, groups=groups)
+    wsb, stb = pipe.sizes
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.Stream()
+    for rep in range(2):                          # a second staging buffer rebinds the plans
+        stage = torch.empty(stb + 256 * rep, dtype=torch.uint8, device="cuda")[256 * rep:]
+        host = [torch.full((len(s) * s.itemsize,), 0xAB, dtype=torch.uint8, pin_memory=True) for s in want]
+        for _ in range(3):                        # runs after the first reuse the bound descriptors
+            pipe.run([h.data_ptr() for h in host], ws, wsb, stage, stb, cs)
+        cs.synchronize()
+        assert pipe.errors() == 0
+        for s, h in zip(want, host):
+            assert np.array_equal(h.numpy().view(s.dtype), s)

@@ -125,3 +125,24 @@ def test_encode_with_given_table_matches_oracle(recoil_lib):
         R.encode_with_table(s, 12, bad, 4)                        # an occurring symbol without probability
     with pytest.raises(R.RecoilError):
         R.encode_with_table(s, 12, f[:-1], 4) if f[-1] else R.encode_with_table(s, 12, f * 2, 4)
+
+
+def test_shard_plans_stage_only_their_word_window(recoil_lib):
+    """A shard plan's workspace holds the words its run reads, not the whole stream: with four
+    ranks each stages about a quarter of the words (plus descriptors); an imported stream, whose
+    lowest-word records are unknown, stages every word from the start of the stream."""
+    R = recoil_lib
+    st = workloads.Stream("z", 3_000_017, 1, 12, "zipf", {"s": 1.2}, seed=91)
+    s = st.symbols()
+    p = R.combine_splits(R.encode_with_splits(s, 12, 512), 64)
+    words = 2 * p.info["n_words"]
+    full = R.Plan([p], {"warps_per_cta": 8}).workspace_size
+    sizes = [R.Plan.shard(p, 4, r, {"warps_per_cta": 8})[0].workspace_size for r in range(4)]
+    assert all(sz < full - words // 2 for sz in sizes), (sizes, full, words)
+    assert sum(sizes) < full + words // 4 + 4 * (full - words)
+    e = p.export()
+    imp = R.stream_import(12, 1, len(s), e["freq"], e["words"], e["final"], e["entry_word"], e["entry_index"],
+                          e["entry_state"])
+    imp_sizes = [R.Plan.shard(imp, 4, r, {"warps_per_cta": 8})[0].workspace_size for r in range(4)]
+    assert imp_sizes[0] == sizes[0] and all(a > b for a, b in zip(imp_sizes[1:], sizes[1:]))
+    assert imp_sizes[3] >= words

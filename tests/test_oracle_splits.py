@@ -161,3 +161,18 @@ def test_config1_split_decodes_and_combines():
     sync = int((o.idx[:-1].max(axis=1) - mins).max()) + 32
     owned = np.diff(np.concatenate([[0], mins, [len(s)]]))
     assert np.all(np.abs(owned - T) <= 2 * sync)
+
+
+@pytest.mark.parametrize("M", [4, 32])
+def test_lowest_word_read_by_a_thread(M):
+    """A thread that stops at symbol lo reads no word below the first word whose renormalisation
+    event is at a symbol >= lo (decoding mirrors encoding word for word), and does read that one:
+    shard plans stage words from there on."""
+    st = workloads.Stream("z", 200_003, 1, 12, "zipf", {"s": 1.2}, seed=90).symbols()
+    o = oracle.encode_with_splits(st, 12, M)
+    for k in range(1, o.K):
+        lo, hi = oracle.owned_range(o, k)
+        out, tr, tw = oracle.decode_thread(o, k, trace=True)
+        read = tw[tw >= 0]
+        want = int(np.searchsorted(o.ev_sym, lo, side="left"))
+        assert read.min() == want, (k, read.min(), want)
