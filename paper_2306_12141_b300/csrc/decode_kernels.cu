@@ -323,9 +323,10 @@ struct EntryDecoder {
       while (g - 7 >= steady_lo) {
         const int rp0 = w.rp;
         const int i0 = g * kW + lane;
-        // adaptive: table numbers of the block after next into L1 (256 bytes, 8 per lane)
+        // adaptive: table numbers of the block after next into L1 (256 bytes, 8 per lane),
+        // only of groups this walk decodes (a shard plan stages no others)
         if constexpr (is_adaptive<KIND>())
-          if (g >= 23) prefetch_l1(tid + (g - 23) * kW + lane * 8);
+          if (g - 23 >= steady_lo) prefetch_l1(tid + (g - 23) * kW + lane * 8);
 #pragma unroll
         for (int u = 0; u < 8; ++u) sstep(w, o - u * kW, i0 - u * kW);
         o -= 8 * kW;

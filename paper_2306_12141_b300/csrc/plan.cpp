@@ -174,7 +174,8 @@ struct recoil_plan {
   size_t off_tables = 0, off_meta = 0, ws_bytes = 0;   // words start at 0
   std::vector<uint64_t> word_off;                      // per stream: its staged words' place in the pool, in words
   std::vector<uint64_t> word_lo, word_cnt;             // per stream: first staged word and how many are staged
-  std::vector<uint64_t> tid_off;                       // per adaptive stream: its table numbers, in words
+  std::vector<uint64_t> tid_off;                       // per adaptive stream: its staged table numbers, in words
+  std::vector<uint64_t> tid_lo, tid_cnt;               // per adaptive stream: first staged symbol and how many
   uint32_t n_items = 0;
   uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {}, kind_warp_queue[kKinds] = {};
   std::vector<uint32_t> stream_kind, stream_item_first, stream_item_count;
@@ -220,6 +221,8 @@ static int plan_build(recoil_plan* P) {
   P->word_lo.assign(count, 0);
   P->word_cnt.assign(count, 0);
   P->tid_off.assign(count, 0);
+  P->tid_lo.assign(count, 0);
+  P->tid_cnt.assign(count, 0);
   P->stream_kind.resize(count);
   std::vector<std::pair<size_t, const std::vector<uint8_t>*>> tabs;
   for (uint32_t i = 0; i < count; i++) {
@@ -260,13 +263,34 @@ static int plan_build(recoil_plan* P) {
     table_off += img.size();
     word_off += align_up(whi - wlo, kChunkWords);
     if (s.adaptive()) {
-      // the table numbers follow the words, one byte per symbol, on a chunk boundary
-      d.tid = word_off;
+      // the table numbers follow the words, one byte per symbol, on a chunk
+      // boundary; a shard plan stages those of the symbols its run decodes,
+      // from its low end to the highest recorded index of its last split
+      uint64_t tlo = 0, thi = s.n_syms;
+      if (P->shard) {
+        const uint32_t K = (uint32_t)s.entries.size() + 1;
+        if (P->entry_first >= P->entry_last) {
+          thi = 0;
+        } else {
+          if (P->entry_first > 0) {
+            const Entry& e = s.entries[P->entry_first - 1];
+            tlo = *std::min_element(e.idx, e.idx + kW) / (2 * kChunkWords) * (2 * kChunkWords);
+          }
+          if (P->entry_last < K) {
+            const Entry& e = s.entries[P->entry_last - 1];
+            thi = std::min<uint64_t>(s.n_syms, (uint64_t)*std::max_element(e.idx, e.idx + kW) + 1);
+          }
+          if (thi < tlo) thi = tlo;
+        }
+      }
+      d.tid = (int64_t)word_off - (int64_t)(tlo / 2);
       d.row_stride = adaptive_row_stride(s.alphabet());
       d.n_tables = s.n_tables;
       d.guide_stride = adaptive_kind_guided(kind) ? guide_stride(s.n_bits) : 0;
       P->tid_off[i] = word_off;
-      word_off += align_up((s.n_syms + 1) / 2, kChunkWords);
+      P->tid_lo[i] = tlo;
+      P->tid_cnt[i] = thi - tlo;
+      word_off += align_up((thi - tlo + 1) / 2, kChunkWords);
     }
     P->kind_smem[kind] = std::max<uint32_t>(P->kind_smem[kind], d.table_bytes);
     if (s.adaptive() && !adaptive_warps_supported(warps))
@@ -437,8 +461,8 @@ cudaError_t plan_upload_stream(const recoil_plan* P, size_t i, uint8_t* ws, cuda
   if (P->word_cnt[i])
     e = cudaMemcpyAsync(ws + P->word_off[i] * 2, s.word_data() + P->word_lo[i], P->word_cnt[i] * 2,
                         cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess && s.adaptive() && s.n_syms)
-    e = cudaMemcpyAsync(ws + P->tid_off[i] * 2, s.tid->data(), s.n_syms, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && s.adaptive() && P->tid_cnt[i])
+    e = cudaMemcpyAsync(ws + P->tid_off[i] * 2, s.tid->data() + P->tid_lo[i], P->tid_cnt[i], cudaMemcpyHostToDevice, cs);
   return e;
 }
 
@@ -456,7 +480,7 @@ void plan_bulk_image(const recoil_plan* P, uint8_t* dst) {
   for (size_t i = 0; i < P->streams.size(); i++) {
     const Stream& s = *P->streams[i];
     if (P->word_cnt[i]) std::memcpy(dst + P->word_off[i] * 2, s.word_data() + P->word_lo[i], P->word_cnt[i] * 2);
-    if (s.adaptive() && s.n_syms) std::memcpy(dst + P->tid_off[i] * 2, s.tid->data(), s.n_syms);
+    if (s.adaptive() && P->tid_cnt[i]) std::memcpy(dst + P->tid_off[i] * 2, s.tid->data() + P->tid_lo[i], P->tid_cnt[i]);
   }
   if (!P->tables.empty()) std::memcpy(dst + P->off_tables, P->tables.data(), P->tables.size());
 }

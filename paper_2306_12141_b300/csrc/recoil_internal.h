@@ -99,7 +99,8 @@ static_assert(sizeof(DevEntry) == 32 + 8 * kW, "DevEntry layout");
 struct alignas(16) DevStream {
   uint64_t words;            // element offset of the stream's words in the word pool (multiple of 256)
   uint64_t table;            // byte offset of the stream's tables in the table pool (multiple of 16)
-  uint64_t tid;              // adaptive: element offset (16-bit units) of its table-number bytes in the word pool
+  int64_t tid;               // adaptive: element offset (16-bit units) in the word pool of the table number of
+                             // symbol 0 (a shard plan stages a window of them, so this may point before it)
   uint32_t n_words;
   uint32_t n_bits;
   uint32_t kind;             // TableKind

@@ -146,3 +146,15 @@ def test_shard_plans_stage_only_their_word_window(recoil_lib):
     imp_sizes = [R.Plan.shard(imp, 4, r, {"warps_per_cta": 8})[0].workspace_size for r in range(4)]
     assert imp_sizes[0] == sizes[0] and all(a > b for a, b in zip(imp_sizes[1:], sizes[1:]))
     assert imp_sizes[3] >= words
+
+
+def test_adaptive_shard_plans_stage_a_window_of_table_numbers(recoil_lib):
+    R = recoil_lib
+    a = workloads.AdaptiveStream("t", 2_000_003, seed=92)
+    tables = a.tables()
+    s, tid = a.draw()
+    p = R.combine_splits(R.encode_adaptive(s, 16, tables, tid, 512), 64)
+    full = R.Plan([p], {"warps_per_cta": 8}).workspace_size
+    sizes = [R.Plan.shard(p, 4, r, {"warps_per_cta": 8})[0].workspace_size for r in range(4)]
+    staged = 2 * p.info["n_words"] + len(s)               # words + one table number per symbol
+    assert all(sz < full - staged // 2 for sz in sizes), (sizes, full, staged)
