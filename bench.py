@@ -676,7 +676,8 @@ def run_ours(a):
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_bytes),
                    "ms_per_step": statistics.mean(e_ms), "groups": a.e2e_groups,
                    "note": "recoil_pipeline_run: H2D of words (+ descriptors, tables), decode, D2H of the symbols, "
-                           "overlapped across stream groups"}
+                           "overlapped across stream groups (a stream larger than its share is cut into runs "
+                           "of splits)"}
             del pws, stage
 
     mean_ms, total_bytes = aggregate(statistics.mean(ms), out_bytes, dev if dist else None)
