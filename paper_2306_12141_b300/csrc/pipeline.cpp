@@ -102,15 +102,15 @@ int recoil_pipeline_create(const recoil_stream* const* streams, uint32_t count, 
     if (opts) run_opts = *opts;
     run_opts.split_symbols = 0;
     uint64_t acc = 0;
-    bool open = false;
+    bool group_open = false;
     cudaError_t e = cudaSuccess;
     for (uint32_t i = 0; i < count; i++) {
       const recoil_stream* s = streams[i];
       const uint64_t runs = P->out_bytes[i] / share;
       if (runs < 2) {
-        if (!open) {
+        if (!group_open) {
           P->groups.emplace_back();
-          open = true;
+          group_open = true;
           acc = 0;
         }
         Group& G = P->groups.back();
@@ -118,10 +118,10 @@ int recoil_pipeline_create(const recoil_stream* const* streams, uint32_t count, 
         G.out_len.push_back(P->out_bytes[i]);
         G.host_off.push_back(0);
         acc += P->out_bytes[i];
-        if (acc >= share) open = false;
+        if (acc >= share) group_open = false;
         continue;
       }
-      open = false;
+      group_open = false;
       const recoil_stream* src = s;
       if (opts && opts->split_symbols) {
         // the split size the caller asked for, rounded to whole CTAs, before cutting into runs
