@@ -91,20 +91,21 @@ struct Tables {
 // modulo 2^16 and exact since every f of an adaptive model is below 2^16.
 //
 // GUIDED (alphabets up to 256): the row's guide holds, for each of 2^g equal
-// buckets of slots, the symbols owning the bucket's first slot (low byte) and
-// the next bucket's first slot (high byte); the symbol of `slot` lies between
-// the two, and a binary search narrows that range (usually empty: one
-// lookup). Otherwise a 12-step binary search over the whole row.
+// buckets of slots, the symbol owning the bucket's first slot (one byte),
+// then the owner of the last slot; the symbol of `slot` lies between the
+// entries of its bucket and the next, and a binary search narrows that range
+// (usually empty: one lookup). Otherwise a 12-step binary search over the
+// whole row.
 template <bool GUIDED>
 struct AdaptiveTables {
   const uint16_t* cdf;
-  const uint16_t* guide;
+  const uint8_t* guide;
   uint32_t stride, gstride, gshift, A;
   __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream& st) {
     cdf = reinterpret_cast<const uint16_t*>(smem);
-    guide = reinterpret_cast<const uint16_t*>(smem + (size_t)st.n_tables * st.row_stride * 2);
+    guide = smem + (size_t)st.n_tables * st.row_stride * 2;
     stride = st.row_stride;
-    gstride = st.guide_stride / 2;
+    gstride = st.guide_stride;
     gshift = st.n_bits > kGuideBits ? st.n_bits - kGuideBits : 0;
     A = st.alphabet;
   }
@@ -113,9 +114,9 @@ struct AdaptiveTables {
     const uint16_t* row = cdf + t * stride;
     uint32_t s;
     if (GUIDED) {
-      const uint32_t pair = guide[t * gstride + (slot >> gshift)];
-      s = pair & 0xffu;
-      uint32_t hi = pair >> 8;
+      const uint8_t* gb = guide + t * gstride + (slot >> gshift);
+      s = gb[0];
+      uint32_t hi = gb[1];
       while (s < hi) {                                  // bounded: hi - s halves
         const uint32_t mid = (s + hi + 1) >> 1;
         if (row[mid] < slot) s = mid; else hi = mid - 1;

@@ -42,10 +42,10 @@ uint32_t adaptive_row_stride(uint32_t A) {
 
 uint32_t guide_bits(uint32_t n) { return std::min<uint32_t>(kGuideBits, n); }
 
-// Bytes between guide rows: 2^g two-byte entries, an odd number of 32-bit
-// words (rows start in different banks).
+// Bytes between guide rows: 2^g + 1 one-byte entries, an odd number of
+// 32-bit words (rows start in different banks).
 uint32_t guide_stride(uint32_t n) {
-  uint32_t words = std::max<uint32_t>(1, (1u << guide_bits(n)) / 2);
+  uint32_t words = ((1u << guide_bits(n)) + 1 + 3) / 4;
   if (!(words & 1)) words++;
   return 4 * words;
 }
@@ -60,30 +60,28 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
     if (is_adaptive_kind(k)) {
       // one row per PDF: H(s) = F(s) - 1 modulo 2^16 for s = 0..A (H(0) = 0xffff,
       // H(A) = 2^n - 1); guided kinds then add a guide row per PDF: for each of
-      // the 2^g buckets of slots, the symbols owning its first slot and the
-      // next bucket's first slot (the last slot for the last bucket), one byte each
+      // the 2^g buckets of slots the symbol owning its first slot, one byte,
+      // and after them the owner of the last slot, so that entries b and b + 1
+      // bracket the symbol of any slot in bucket b
       const uint32_t stride = adaptive_row_stride(A);
       const size_t rows_bytes = (size_t)s.n_tables * stride * 2;
       const bool guided = adaptive_kind_guided(k);
       const uint32_t gb = guide_bits(n), gstride = guide_stride(n);
       s.table_img.assign(align_up(rows_bytes + (guided ? (size_t)s.n_tables * gstride : 0), 16), 0);
       uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data());
-      uint16_t* guide = reinterpret_cast<uint16_t*>(s.table_img.data() + rows_bytes);
+      uint8_t* guide = s.table_img.data() + rows_bytes;
       std::vector<uint32_t> F(A + 1);
       for (uint32_t t = 0; t < s.n_tables; t++) {
         F[0] = 0;
         for (uint32_t sym = 0; sym < A; sym++) F[sym + 1] = F[sym] + s.freq[(size_t)t * A + sym];
         for (uint32_t sym = 0; sym <= A; sym++) cdf[(size_t)t * stride + sym] = (uint16_t)(F[sym] - 1);
         if (!guided) continue;
-        std::vector<uint32_t> first((1u << gb) + 1);
         uint32_t sym = 0;
         for (uint32_t b = 0; b <= (1u << gb); b++) {
           const uint32_t slot = std::min<uint32_t>(b << (n - gb), (1u << n) - 1);
           while (F[sym + 1] <= slot) sym++;              // the symbol whose slots hold `slot`
-          first[b] = sym;
+          guide[(size_t)t * gstride + b] = (uint8_t)sym;
         }
-        for (uint32_t b = 0; b < (1u << gb); b++)
-          guide[(size_t)t * (gstride / 2) + b] = (uint16_t)(first[b] | first[b + 1] << 8);
       }
     } else if (k == kPacked8) {
       s.table_img.assign(align_up((size_t)slots * 4, 16), 0);

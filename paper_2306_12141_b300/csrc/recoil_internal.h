@@ -38,8 +38,8 @@ enum TableKind : uint32_t {
 __host__ __device__ constexpr bool is_adaptive_kind(uint32_t k) { return k >= kAdaptive8 && k < kKinds; }
 // Kinds whose rows come with a bucket guide (alphabets up to 256: one byte per bucket).
 __host__ __device__ constexpr bool adaptive_kind_guided(uint32_t k) { return k == kAdaptive8 || k == kAdaptive16; }
-// The guide of a row: 2^g buckets over the 2^n slots, g = min(8, n).
-constexpr uint32_t kGuideBits = 8;
+// The guide of a row: 2^g buckets over the 2^n slots, g = min(9, n).
+constexpr uint32_t kGuideBits = 9;
 
 // Longest alphabet of an adaptive model (the decoder's CDF search covers 2^12 symbols).
 constexpr uint32_t kMaxAdaptiveAlphabet = 4096;
@@ -110,7 +110,7 @@ struct alignas(16) DevStream {
   uint32_t slot_bytes;       // generic kinds: bytes of the slot -> symbol part (multiple of 16)
   uint32_t row_stride;       // adaptive: 16-bit entries between CDF rows (odd number of 32-bit words)
   uint32_t n_tables;         // adaptive: CDF rows
-  uint32_t guide_stride;     // guided adaptive kinds: bytes between guide rows (after all CDF rows; 2 B per bucket)
+  uint32_t guide_stride;     // guided adaptive kinds: bytes between guide rows (after all CDF rows; 1 B per bucket boundary)
 };
 static_assert(sizeof(DevStream) == 64, "DevStream layout");
 
