@@ -154,6 +154,13 @@ def recorded_traffic(key: str):
     return None
 
 
+def kernel_of(info: dict) -> tuple[str, str]:
+    """(symbol dtype, decode kernel) of a static-model stream, as the plan picks its tables."""
+    if info["sym_bytes"] == 2:
+        return "u16", "decode_kernel<kGeneric16>"
+    return "u8", "decode_kernel<kPacked8>" if info["n_bits"] <= 12 else "decode_kernel<kGeneric8>"
+
+
 NOMINAL_HBM_GBS = 8000.0      # HBM3e nominal (~8 TB/s), a second denominator beside the measured copy
 
 
@@ -687,10 +694,11 @@ def run_ours(a):
     tkey = (f"batch w{opts['warps_per_cta']} s{split_symbols}" if batch
             else f"{a.dist} w{opts['warps_per_cta']} k{a.splits}")
     traffic = recorded_traffic(tkey) if a.scale == 1.0 and a.streams == workloads.BATCH_STREAMS else None
+    dtype, kernel = kernel_of(plan.streams[0].info)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": desc, "symbols_bytes": out_bytes, "compressed_bytes": in_bytes,
                    "splits": sum(st.info["n_entries"] for st in plan.streams) if not batch else None,
                    "split_symbols": split_symbols, "warps_per_cta": opts["warps_per_cta"],
@@ -702,7 +710,7 @@ def run_ours(a):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"],
                      "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                     "kernel": "decode_kernel<kPacked8>", "bytes": "compressed words in + symbols out"},
+                     "kernel": kernel, "bytes": "compressed words in + symbols out"},
         "clocks": clocks,
         "gpu_launches": launches * a.steps,
         "e2e": e2e,

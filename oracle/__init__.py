@@ -62,7 +62,7 @@ def lib():
         L.oracle_scan.argtypes = [p, p, i64, i32, p, p, p]
         L.oracle_heuristic.argtypes = [p, p, i64, i64, i32, i64, p]
         L.oracle_heuristic.restype = i64
-        L.oracle_combine.argtypes = [i64, i64, p]
+        L.oracle_combine.argtypes = [i64, i64, p, i64, p]
         L.oracle_combine.restype = i64
         L.oracle_decode_thread.argtypes = [p, i64, p, i64, p, i32, i32, i32, i32, i32,
                                            i32, p, p, i64, i64, i64, p, p, p]
@@ -198,9 +198,12 @@ def heuristic(ev_sym, ev_y, N: int, M: int, W: int = W_DEFAULT) -> np.ndarray:
     return q[:k].copy()
 
 
-def combine_keep(K: int, Mp: int) -> np.ndarray:
+def combine_keep(m, N: int, Mp: int) -> np.ndarray:
+    """Kept entry numbers when combining to Mp (m: owned ends of the K-1 regular entries)."""
+    mm = _i64(np.asarray(m, dtype=np.int64))
+    K = len(mm) + 1
     keep = np.zeros(max(1, min(K, Mp)), dtype=np.int64)
-    k = lib().oracle_combine(K, Mp, _ptr(keep))
+    k = lib().oracle_combine(K, Mp, _ptr(mm) if len(mm) else None, N, _ptr(keep))
     if k < 0:
         raise ValueError("oracle_combine failed")
     return keep[:k].copy()
@@ -270,7 +273,7 @@ def encode_adaptive_with_splits(sym, tid, tables, n: int, M: int, W: int = W_DEF
 
 def combined(st: OracleStream, Mp: int) -> OracleStream:
     """The same stream with only Mp entries kept (the final entry always stays)."""
-    keep = combine_keep(st.K, Mp)
+    keep = combine_keep(st.idx[:-1].min(axis=1) if st.K > 1 else [], st.N, Mp)
     regular = [k for k in keep if k < st.K - 1]
     return OracleStream(st.N, st.n, st.W, st.lgL, st.b, st.f, st.words, st.final, st.ev_sym,
                         st.ev_y, st.q[regular], np.vstack([st.idx[regular], st.idx[-1:]]),

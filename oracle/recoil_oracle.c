@@ -39,7 +39,11 @@
  *   - An entry is usable only if every coder has such a record with index >= 0.
  *   - Thread k owns symbols [m_{k-1}, m_k - 1], m = smallest recorded index of
  *     an entry, m_{-1} = 0, and the final entry owns up to N - 1.
- *   - Combining keeps entries ceil((k+1) K / M') - 1, k = 0..M'-1.
+ *   - Combining (Sec. 3.3 wants bigger splits with close symbol counts) keeps,
+ *     for k = 0..M'-2, the entry whose owned end m is nearest to
+ *     floor((k+1) N / M'), searching after the previous kept entry and leaving
+ *     one entry for each later target (ties: the smaller m, then the earlier
+ *     entry), and always the final entry.
  *   - Heuristic ties go to the smaller word offset.
  *
  * All arithmetic is integer and exact; states are held in 64-bit integers so
@@ -392,11 +396,30 @@ int64_t oracle_heuristic(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw
     return count;
 }
 
-/* Combining (Sec. 3.3, 4.2): keep entries ceil((k+1) K / Mp) - 1, k = 0..Mp-1. */
-int64_t oracle_combine(int64_t K, int64_t Mp, int64_t *keep) {
-    if (K < 1 || Mp < 1) return OR_EINVAL;
+/*
+ * Combining (Sec. 3.3, 4.2): of K entries (K-1 regular ones, owned ends
+ * m[0..K-2] non-decreasing, then the final entry) keep Mp. Split k of the
+ * result should own about N / Mp symbols, so for k = 0..Mp-2 take, among the
+ * entries after the previous kept one that still leave one entry for each
+ * later target, the first whose m is nearest to floor((k+1) N / Mp); the
+ * final entry (index K-1) is always kept.
+ */
+int64_t oracle_combine(int64_t K, int64_t Mp, const int64_t *m, int64_t N, int64_t *keep) {
+    if (K < 1 || Mp < 1 || N < 0) return OR_EINVAL;
     if (Mp > K) Mp = K;
-    for (int64_t k = 0; k < Mp; k++) keep[k] = ((k + 1) * K + Mp - 1) / Mp - 1;
+    int64_t first = 0;
+    for (int64_t k = 0; k + 1 < Mp; k++) {
+        const int64_t last = (K - 1) - (Mp - 1 - k);          /* room for Mp-2-k more */
+        const int64_t target = (int64_t)((__int128)(k + 1) * N / Mp);
+        int64_t best = -1, best_d = 0;
+        for (int64_t e = first; e <= last; e++) {
+            const int64_t d = m[e] > target ? m[e] - target : target - m[e];
+            if (best < 0 || d < best_d) { best = e; best_d = d; }
+        }
+        keep[k] = best;
+        first = best + 1;
+    }
+    keep[Mp - 1] = K - 1;
     return Mp;
 }
 

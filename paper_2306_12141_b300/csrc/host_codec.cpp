@@ -394,11 +394,32 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_strea
     s->words = in->words;
     s->pinned_words = in->pinned_words;
     std::memcpy(s->final_x, in->final_x, sizeof s->final_x);
-    const uint64_t K = in->entries.size() + 1;
-    const uint64_t Mp = std::min<uint64_t>(target, K);
-    for (uint64_t k = 0; k + 1 < Mp; k++) {                  // the last kept one is the final entry
-      const uint64_t e = ((k + 1) * K + Mp - 1) / Mp - 1;
-      s->entries.push_back(in->entries[e]);
+    // Sec. 3.3: the combined splits should own close symbol counts. For split
+    // k the kept entry is the one whose owned end (smallest recorded index)
+    // lies nearest to (k+1) N / Mp, searched after the previous kept entry and
+    // leaving one entry for each later split (ties: the smaller end, then the
+    // earlier entry); the final entry is always kept. Owned ends never
+    // decrease, so each choice is a binary search.
+    const uint64_t R = in->entries.size();                    // regular entries
+    const uint64_t Mp = std::min<uint64_t>(target, R + 1);
+    std::vector<uint64_t> m(R);
+    for (uint64_t e = 0; e < R; e++) m[e] = *std::min_element(in->entries[e].idx, in->entries[e].idx + kW);
+    uint64_t first = 0;
+    for (uint64_t k = 0; k + 1 < Mp; k++) {
+      const uint64_t last = R - (Mp - 1 - k);
+      const uint64_t t = (uint64_t)((unsigned __int128)(k + 1) * in->n_syms / Mp);
+      const auto lo = m.begin() + first, hi = m.begin() + last + 1;
+      const uint64_t b = std::lower_bound(lo, hi, t) - m.begin();  // first end >= t
+      uint64_t pick;
+      if (b == first) {
+        pick = b;
+      } else {
+        const uint64_t a = m[b - 1];                                // the largest end below t
+        if (b <= last && m[b] - t < t - a) pick = b;
+        else pick = std::lower_bound(lo, m.begin() + b, a) - m.begin();
+      }
+      s->entries.push_back(in->entries[pick]);
+      first = pick + 1;
     }
     *out = s.release();
     return RECOIL_OK;

@@ -68,8 +68,8 @@ def test_combine_matches_oracle_rule(recoil_lib, K, Mp):
     p = recoil_lib.encode_with_splits(s, 11, K)
     assert p.info["n_entries"] == K
     c = recoil_lib.combine_splits(p, Mp)
-    keep = oracle.combine_keep(K, Mp)
     ep, ec = p.export(), c.export()
+    keep = oracle.combine_keep(ep["entry_index"].astype(np.int64).min(axis=1), len(s), Mp)
     regular = [k for k in keep if k < K - 1]
     assert c.info["n_entries"] == len(keep)
     assert np.array_equal(ec["entry_word"], ep["entry_word"][regular])

@@ -134,14 +134,49 @@ def test_heuristic_attains_minimum_of_eq7(dist, params, n, M):
     assert st.K <= M
 
 
-@pytest.mark.parametrize("K,Mp", [(64, 16), (64, 1), (64, 64), (65536, 148), (10, 3), (7, 20)])
+@pytest.mark.parametrize("K,Mp", [(64, 16), (64, 1), (64, 64), (65536, 148), (10, 3), (7, 20), (9, 9)])
 def test_combine_keep_rule(K, Mp):
-    keep = oracle.combine_keep(K, Mp)
+    """Sec. 3.3: on evenly spaced splits, keeping the entries nearest to equal
+    symbol counts is the paper's simple rule, every (K/M')-th entry."""
+    N = 1000 * K
+    m = np.arange(1, K) * 1000                      # regular entry e owns [1000 e, 1000 (e + 1))
+    keep = oracle.combine_keep(m, N, Mp)
     assert len(keep) == min(K, Mp)
     assert keep[-1] == K - 1
     assert np.all(np.diff(keep) > 0)
     if Mp <= K and K % Mp == 0:
         assert keep.tolist() == list(range(K // Mp - 1, K, K // Mp))
+
+
+def test_combine_keep_hand_cases():
+    # nearest owned end wins
+    assert oracle.combine_keep([10, 19, 33], 40, 2).tolist() == [1, 3]
+    # equidistant ends: the smaller one, and the first of equal ends
+    assert oracle.combine_keep([10, 10, 30], 40, 2).tolist() == [0, 3]
+    # each later target keeps an entry of its own
+    assert oracle.combine_keep([5, 6, 7, 100], 200, 4).tolist() == [1, 2, 3, 4]
+    # a target past every end takes the last entry that still leaves room
+    assert oracle.combine_keep([1, 2, 3, 4, 5], 1000, 3).tolist() == [3, 4, 5]
+    # nothing to combine
+    assert oracle.combine_keep([], 7, 5).tolist() == [0]
+
+
+def test_combine_balances_uneven_splits():
+    """Sec. 3.3 asks for combined splits of close symbol counts. Splits encoded
+    on a skewed source own fewer symbols than T early on (long synchronisation
+    sections) and more towards the end; every ceil(K/M')-th entry would pass
+    that drift on, the nearest-end rule does not."""
+    s = workloads.Stream("sk", 1 << 20, 1, 12, "skewed", {"p0": 0.95}, seed=3).symbols()
+    o = oracle.encode_with_splits(s, 12, 256)
+    mins = o.idx[:-1].min(axis=1)
+    enc_owned = np.diff(np.concatenate([[0], mins, [len(s)]]))
+    every = np.diff(np.concatenate([[0], mins[np.arange(1, 16) * o.K // 16 - 1], [len(s)]]))
+    assert enc_owned[-16:].mean() > 1.5 * enc_owned[:16].mean()        # the drift exists
+    assert every.max() > 1.3 * len(s) / 16
+    c = oracle.combined(o, 16)
+    owned = np.diff(np.concatenate([[0], c.idx[:-1].min(axis=1), [len(s)]]))
+    assert np.abs(owned - len(s) / 16).max() <= enc_owned.max()
+    assert np.array_equal(oracle.decode_splits(c), s)
 
 
 def test_config1_split_decodes_and_combines():
