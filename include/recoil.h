@@ -122,7 +122,7 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target_splits, recoi
  *                fit in shared memory with the decoder rings
  *                (n_tables * (alphabet + 1) * 2 bytes, rounded up, <= ~160 KiB)
  * Split placement, combining and plans work as for static streams; adaptive
- * streams decode with 4, 8 or 16 warps per CTA, are not serialised
+ * streams decode with 4, 8, 16 or 32 warps per CTA, are not serialised
  * (recoil_serialize) and not taken by recoil_decode_noalloc.
  * Errors: EINVAL (bad parameters, a row that does not sum to 2^n or has a zero,
  * a table number or symbol out of range), ENOMEM.
@@ -203,9 +203,10 @@ const char* recoil_last_error(void);
 
 /* Batch options. Zero fields take defaults (or the autotuned values). */
 typedef struct {
-  uint32_t warps_per_cta;    /* decoder warps per CTA (1, 2, 4, 8, 16, 32; adaptive streams 4, 8, 16);
+  uint32_t warps_per_cta;    /* decoder warps per CTA (1, 2, 4, 8, 16, 32; adaptive streams 4, 8, 16, 32);
                                 0 = about one CTA round of splits per SM: the power of two
-                                below splits / SMs, clamped to [4, 16] */
+                                below splits / SMs, clamped to [4, 16]; adaptive streams with
+                                64 or more splits per SM take 32 */
   uint32_t ctas_per_sm;      /* persistent CTAs per SM; default: occupancy maximum */
   uint32_t split_symbols;    /* combine each stream to ceil(N / split_symbols) splits; 0 = keep all */
   uint32_t flags;            /* RECOIL_BATCH_* */
@@ -431,9 +432,10 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
 /*
  * Choose batch options for these streams by measurement (the batching pattern
  * of the paper's decoder-adaptive parallelism, Sec. 3.3: the decoder picks the
- * split count that suits it). Candidates: warps_per_cta in {4, 8, 16} times
- * split_symbols in {32 Ki, 64 Ki, 128 Ki, 256 Ki} (with RECOIL_TUNE_KEEP_SPLITS:
- * warps_per_cta in {4, 8, 16} on the streams as given, split_symbols 0, for a
+ * split count that suits it). Candidates: warps_per_cta in {4, 8, 16} (and 32
+ * when a stream is adaptive) times split_symbols in {32 Ki, 64 Ki, 128 Ki,
+ * 256 Ki} (with RECOIL_TUNE_KEEP_SPLITS: those warps_per_cta on the streams as
+ * given, split_symbols 0, for a
  * decoder whose split count is already chosen). Each candidate decodes the
  * streams into d_outs (caller-owned, as for recoil_plan_decode) once untimed
  * and `steps` times timed with CUDA events on cuda_stream; the lowest median

@@ -106,7 +106,7 @@ struct AdaptiveTables {
     guide = smem + (size_t)st.n_tables * st.row_stride * 2;
     stride = st.row_stride;
     gstride = st.guide_stride;
-    gshift = st.n_bits > kGuideBits ? st.n_bits - kGuideBits : 0;
+    gshift = st.n_bits > st.guide_bits ? st.n_bits - st.guide_bits : 0;
     A = st.alphabet;
   }
   __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask, uint32_t t) const {
@@ -483,7 +483,7 @@ int occupancy_kw(uint32_t table_smem, int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
 }
 
-// Static kinds come in every CTA size, adaptive kinds in 4, 8 and 16 warps.
+// Static kinds come in every CTA size, adaptive kinds in 4, 8, 16 and 32 warps.
 template <uint32_t KIND>
 cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   if constexpr (is_adaptive<KIND>()) {
@@ -491,6 +491,7 @@ cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
       case 4: return launch_kw<KIND, 4>(a, grid, s);
       case 8: return launch_kw<KIND, 8>(a, grid, s);
       case 16: return launch_kw<KIND, 16>(a, grid, s);
+      case 32: return launch_kw<KIND, 32>(a, grid, s);
     }
   } else {
     switch (a.warps) {
@@ -512,6 +513,7 @@ int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
       case 4: return occupancy_kw<KIND, 4>(table_smem, out);
       case 8: return occupancy_kw<KIND, 8>(table_smem, out);
       case 16: return occupancy_kw<KIND, 16>(table_smem, out);
+      case 32: return occupancy_kw<KIND, 32>(table_smem, out);
     }
   } else {
     switch (warps) {
@@ -530,7 +532,7 @@ int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
 
 bool warps_supported(uint32_t w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32; }
 
-bool adaptive_warps_supported(uint32_t w) { return w == 4 || w == 8 || w == 16; }
+bool adaptive_warps_supported(uint32_t w) { return w == 4 || w == 8 || w == 16 || w == 32; }
 
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   switch (kind) {

@@ -40,14 +40,24 @@ uint32_t adaptive_row_stride(uint32_t A) {
   return 2 * words;
 }
 
-uint32_t guide_bits(uint32_t n) { return std::min<uint32_t>(kGuideBits, n); }
+uint32_t guide_bits(uint32_t n, uint32_t g) { return std::min<uint32_t>(g, n); }
 
 // Bytes between guide rows: 2^g + 1 one-byte entries, an odd number of
 // 32-bit words (rows start in different banks).
-uint32_t guide_stride(uint32_t n) {
-  uint32_t words = ((1u << guide_bits(n)) + 1 + 3) / 4;
+uint32_t guide_stride(uint32_t n, uint32_t g) {
+  uint32_t words = ((1u << guide_bits(n, g)) + 1 + 3) / 4;
   if (!(words & 1)) words++;
   return 4 * words;
+}
+
+// A guided adaptive stream's table image holds two variants, CDF rows then
+// a guide of 2^9 buckets per row, and the same rows with 2^10 buckets; a plan
+// stages one of them. Offset and size of variant g within the image:
+void guided_variant(const Stream& s, uint32_t g, size_t* off, size_t* bytes) {
+  const size_t rows = (size_t)s.n_tables * adaptive_row_stride(s.alphabet()) * 2;
+  const size_t coarse = align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, kGuideBits), 16);
+  *off = g == kGuideBits ? 0 : coarse;
+  *bytes = g == kGuideBits ? coarse : align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, g), 16);
 }
 
 // Decoder tables of a stream (built once and cached on the stream).
@@ -62,26 +72,36 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
       // H(A) = 2^n - 1); guided kinds then add a guide row per PDF: for each of
       // the 2^g buckets of slots the symbol owning its first slot, one byte,
       // and after them the owner of the last slot, so that entries b and b + 1
-      // bracket the symbol of any slot in bucket b
+      // bracket the symbol of any slot in bucket b. Guided kinds hold the rows
+      // twice, once with each guide width (guided_variant).
       const uint32_t stride = adaptive_row_stride(A);
       const size_t rows_bytes = (size_t)s.n_tables * stride * 2;
       const bool guided = adaptive_kind_guided(k);
-      const uint32_t gb = guide_bits(n), gstride = guide_stride(n);
-      s.table_img.assign(align_up(rows_bytes + (guided ? (size_t)s.n_tables * gstride : 0), 16), 0);
-      uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data());
-      uint8_t* guide = s.table_img.data() + rows_bytes;
+      size_t off9 = 0, size9 = align_up(rows_bytes, 16), off10 = 0, size10 = 0;
+      if (guided) {
+        guided_variant(s, kGuideBits, &off9, &size9);
+        guided_variant(s, kGuideBitsFine, &off10, &size10);
+      }
+      s.table_img.assign(guided ? off10 + size10 : size9, 0);
       std::vector<uint32_t> F(A + 1);
-      for (uint32_t t = 0; t < s.n_tables; t++) {
-        F[0] = 0;
-        for (uint32_t sym = 0; sym < A; sym++) F[sym + 1] = F[sym] + s.freq[(size_t)t * A + sym];
-        for (uint32_t sym = 0; sym <= A; sym++) cdf[(size_t)t * stride + sym] = (uint16_t)(F[sym] - 1);
-        if (!guided) continue;
-        uint32_t sym = 0;
-        for (uint32_t b = 0; b <= (1u << gb); b++) {
-          const uint32_t slot = std::min<uint32_t>(b << (n - gb), (1u << n) - 1);
-          while (F[sym + 1] <= slot) sym++;              // the symbol whose slots hold `slot`
-          guide[(size_t)t * gstride + b] = (uint8_t)sym;
+      for (const size_t base : {off9, off10}) {
+        uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data() + base);
+        uint8_t* guide = s.table_img.data() + base + rows_bytes;
+        const uint32_t g = base == off9 ? kGuideBits : kGuideBitsFine;
+        const uint32_t gb = guide_bits(n, g), gstride = guide_stride(n, g);
+        for (uint32_t t = 0; t < s.n_tables; t++) {
+          F[0] = 0;
+          for (uint32_t sym = 0; sym < A; sym++) F[sym + 1] = F[sym] + s.freq[(size_t)t * A + sym];
+          for (uint32_t sym = 0; sym <= A; sym++) cdf[(size_t)t * stride + sym] = (uint16_t)(F[sym] - 1);
+          if (!guided) continue;
+          uint32_t sym = 0;
+          for (uint32_t b = 0; b <= (1u << gb); b++) {
+            const uint32_t slot = std::min<uint32_t>(b << (n - gb), (1u << n) - 1);
+            while (F[sym + 1] <= slot) sym++;              // the symbol whose slots hold `slot`
+            guide[(size_t)t * gstride + b] = (uint8_t)sym;
+          }
         }
+        if (!guided) break;
       }
     } else if (k == kPacked8) {
       s.table_img.assign(align_up((size_t)slots * 4, 16), 0);
@@ -205,10 +225,60 @@ static uint32_t entry_work(const DevEntry& de) {
   return (uint32_t)std::max<int64_t>(0, std::min<int64_t>(span, 0x7fffffff));
 }
 
+static int device_sms();
+
+// CTAs of `warps` warps that one SM holds when each needs `smem` bytes of
+// shared memory; adaptive kernels are built for 32 resident warps an SM
+// (64 registers a thread).
+static uint64_t adaptive_ctas_per_sm(uint32_t warps, size_t smem) {
+  int dev = 0, per_sm = 0, reserved = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();
+    per_sm = 228 * 1024;                           // sm_100 / sm_103
+    reserved = 1024;
+  }
+  return std::min<uint64_t>((uint64_t)per_sm / (smem + (size_t)reserved), 32 / warps);
+}
+
+// Guide width of each guided adaptive kind in a plan: the finer guide (about
+// a third fewer search steps on wide PDFs) unless its larger tables lower the
+// number of the kind's splits that the GPU decodes at once.
+static void choose_guides(const recoil_plan* P, uint32_t* guide) {
+  uint64_t entries[kKinds] = {};
+  size_t coarse[kKinds] = {}, fine[kKinds] = {};
+  for (uint32_t k = 0; k < kKinds; k++) guide[k] = kGuideBits;
+  for (const Stream* s : P->streams) {
+    const uint32_t k = table_kind_of(*s);
+    if (!adaptive_kind_guided(k)) continue;
+    entries[k] += P->shard ? P->entry_last - P->entry_first : s->entries.size() + 1;
+    size_t off = 0, bytes = 0;
+    guided_variant(*s, kGuideBits, &off, &bytes);
+    coarse[k] = std::max(coarse[k], bytes);
+    guided_variant(*s, kGuideBitsFine, &off, &bytes);
+    fine[k] = std::max(fine[k], bytes);
+  }
+  const size_t rings = (size_t)P->warps * ring_smem_per_warp() + 16;
+  const uint64_t sms = (uint64_t)device_sms();
+  for (uint32_t k = 0; k < kKinds; k++) {
+    if (!entries[k] || fine[k] + rings > kMaxSmem) continue;
+    const uint64_t cap9 = adaptive_ctas_per_sm(P->warps, coarse[k] + rings) * sms * P->warps;
+    const uint64_t cap10 = adaptive_ctas_per_sm(P->warps, fine[k] + rings) * sms * P->warps;
+    if (std::min(entries[k], cap10) >= std::min(entries[k], cap9)) guide[k] = kGuideBitsFine;
+  }
+}
+
 static int plan_build(recoil_plan* P) {
   const uint32_t count = (uint32_t)P->streams.size();
   const bool per_stream = P->opts.flags & RECOIL_BATCH_PER_STREAM;
   const uint32_t warps = P->warps;
+  for (const Stream* s : P->streams)
+    if (s->adaptive() && !adaptive_warps_supported(warps))
+      return fail(RECOIL_EINVAL, "adaptive streams decode with 4, 8, 16 or 32 warps per CTA");
+  uint32_t guide[kKinds];
+  choose_guides(P, guide);
   std::vector<DevStream> ds(count);
   std::vector<DevEntry> entries;
   struct ItemK { DevItem it; uint32_t kind; };
@@ -284,15 +354,21 @@ static int plan_build(recoil_plan* P) {
       d.tid = (int64_t)word_off - (int64_t)(tlo / 2);
       d.row_stride = adaptive_row_stride(s.alphabet());
       d.n_tables = s.n_tables;
-      d.guide_stride = adaptive_kind_guided(kind) ? guide_stride(s.n_bits) : 0;
+      if (adaptive_kind_guided(kind)) {
+        // stage the variant of the plan's guide width
+        size_t voff = 0, vbytes = 0;
+        guided_variant(s, guide[kind], &voff, &vbytes);
+        d.table += voff;
+        d.table_bytes = (uint32_t)vbytes;
+        d.guide_bits = guide_bits(s.n_bits, guide[kind]);
+        d.guide_stride = guide_stride(s.n_bits, guide[kind]);
+      }
       P->tid_off[i] = word_off;
       P->tid_lo[i] = tlo;
       P->tid_cnt[i] = thi - tlo;
       word_off += align_up((thi - tlo + 1) / 2, kChunkWords);
     }
     P->kind_smem[kind] = std::max<uint32_t>(P->kind_smem[kind], d.table_bytes);
-    if (s.adaptive() && !adaptive_warps_supported(warps))
-      return fail(RECOIL_EINVAL, "adaptive streams decode with 4, 8 or 16 warps per CTA");
 
     const size_t first = entries.size();
     build_entries(s, i, entries, wlo);
@@ -440,9 +516,12 @@ static int device_sms() {
 // two nearest below splits / SMs, within [4, 16]. Few splits run faster in
 // small CTAs spread over every SM (a split is one warp's dependent chain);
 // measured on 1 GiB Zipf: 148-1184 splits +14-19% against 16-warp CTAs,
-// 2368 and more within 1% of the best size.
-static uint32_t auto_warps(uint64_t splits) {
+// 2368 and more within 1% of the best size. Adaptive streams with 64 or more
+// splits an SM take 32-warp CTAs, one per SM, which leaves room for the finer
+// guide (adaptive latents at 9472 splits: 1000 against 945 GB/s).
+static uint32_t auto_warps(uint64_t splits, bool adaptive) {
   const uint64_t per_sm = splits / (uint64_t)device_sms();
+  if (adaptive && per_sm >= 64) return 32;
   uint32_t w = 4;
   while (w < 16 && (uint64_t)w * 2 <= per_sm) w *= 2;
   return w;
@@ -577,13 +656,15 @@ int recoil_plan_create(const recoil_stream* const* streams, uint32_t count, cons
     P->warps = P->opts.warps_per_cta;
     if (!P->warps) {
       uint64_t splits = 0;
+      bool adaptive = count > 0;
       for (uint32_t i = 0; i < count; i++) {
         if (!streams[i]) return fail(RECOIL_EINVAL, "null stream");
         splits += P->opts.split_symbols
                       ? std::max<uint64_t>(1, (streams[i]->n_syms + P->opts.split_symbols - 1) / P->opts.split_symbols)
                       : streams[i]->entries.size() + 1;
+        adaptive = adaptive && streams[i]->adaptive();
       }
-      P->warps = auto_warps(splits);
+      P->warps = auto_warps(splits, adaptive);
     }
     if (!warps_supported(P->warps)) return fail(RECOIL_EINVAL, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
     for (uint32_t i = 0; i < count; i++) {
@@ -761,7 +842,7 @@ int recoil_plan_create_shard(const recoil_stream* s, uint32_t world, uint32_t ra
     if (first >= last) *sym_hi = *sym_lo;
     std::unique_ptr<recoil_plan> P(new recoil_plan());
     if (opts) P->opts = *opts;
-    P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta : auto_warps(std::max(first, last) - first);
+    P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta : auto_warps(std::max(first, last) - first, s->adaptive());
     if (!warps_supported(P->warps)) return fail(RECOIL_EINVAL, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
     P->streams.push_back(s);
     P->shard = true;

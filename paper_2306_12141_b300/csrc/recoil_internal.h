@@ -38,8 +38,10 @@ enum TableKind : uint32_t {
 __host__ __device__ constexpr bool is_adaptive_kind(uint32_t k) { return k >= kAdaptive8 && k < kKinds; }
 // Kinds whose rows come with a bucket guide (alphabets up to 256: one byte per bucket).
 __host__ __device__ constexpr bool adaptive_kind_guided(uint32_t k) { return k == kAdaptive8 || k == kAdaptive16; }
-// The guide of a row: 2^g buckets over the 2^n slots, g = min(9, n).
+// The guide of a row: 2^g buckets over the 2^n slots, g = min(9, n), or
+// min(10, n) where a plan can afford twice the guide's shared memory.
 constexpr uint32_t kGuideBits = 9;
+constexpr uint32_t kGuideBitsFine = 10;
 
 // Longest alphabet of an adaptive model (the decoder's CDF search covers 2^12 symbols).
 constexpr uint32_t kMaxAdaptiveAlphabet = 4096;
@@ -107,7 +109,10 @@ struct alignas(16) DevStream {
   uint32_t alphabet;
   uint32_t sym_bytes;
   uint32_t table_bytes;      // bytes of the table image (multiple of 16)
-  uint32_t slot_bytes;       // generic kinds: bytes of the slot -> symbol part (multiple of 16)
+  union {
+    uint32_t slot_bytes;     // generic kinds: bytes of the slot -> symbol part (multiple of 16)
+    uint32_t guide_bits;     // guided adaptive kinds: log2 of the guide buckets per row
+  };
   uint32_t row_stride;       // adaptive: 16-bit entries between CDF rows (odd number of 32-bit words)
   uint32_t n_tables;         // adaptive: CDF rows
   uint32_t guide_stride;     // guided adaptive kinds: bytes between guide rows (after all CDF rows; 1 B per bucket boundary)
@@ -167,7 +172,7 @@ cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cud
 int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out);
 size_t ring_smem_per_warp();
 bool warps_supported(uint32_t warps);   // CTA sizes the kernels are built for: 1, 2, 4, 8, 16, 32 warps
-bool adaptive_warps_supported(uint32_t warps);   // adaptive kinds: 4, 8, 16 warps
+bool adaptive_warps_supported(uint32_t warps);   // adaptive kinds: 4, 8, 16, 32 warps
 
 // Host images of a plan (plan.cpp), for entry points that place them in
 // device memory of their own. meta = control, output pointers, stream

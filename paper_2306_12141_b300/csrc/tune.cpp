@@ -20,13 +20,16 @@
 namespace recoil {
 namespace {
 
-const uint32_t kWarps[] = {4, 8, 16};
+const uint32_t kWarps[] = {4, 8, 16, 32};
 const uint32_t kSplit[] = {32768, 65536, 131072, 262144};
 
-// Candidate options: warps x split sizes, or warps alone on the streams' own splits.
-std::vector<recoil_batch_opts> candidates(bool keep_splits) {
+// Candidate options: warps x split sizes, or warps alone on the streams' own
+// splits. 32-warp CTAs only for adaptive streams (one CTA an SM leaves room
+// for the finer guide); static kinds keep 4 to 16.
+std::vector<recoil_batch_opts> candidates(bool keep_splits, bool adaptive) {
   std::vector<recoil_batch_opts> c;
   for (uint32_t w : kWarps) {
+    if (w == 32 && !adaptive) continue;
     if (keep_splits) {
       c.push_back(recoil_batch_opts{w, 0, 0, 0});
       continue;
@@ -89,6 +92,12 @@ struct Candidate {
   recoil_plan* plan = nullptr;
 };
 
+bool any_adaptive(const recoil_stream* const* s, uint32_t count) {
+  for (uint32_t i = 0; i < count; i++)
+    if (s && s[i] && s[i]->adaptive()) return true;
+  return false;
+}
+
 }  // namespace
 }  // namespace recoil
 
@@ -101,7 +110,7 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
   if (!bytes) return fail(RECOIL_EINVAL, "null argument");
   size_t mx = 0;
   for (bool keep : {false, true})
-    for (recoil_batch_opts o : candidates(keep)) {
+    for (recoil_batch_opts o : candidates(keep, any_adaptive(streams, count))) {
       size_t b = 0;
       int rc = recoil_workspace_size(streams, count, &o, &b);
       if (rc) return rc;
@@ -134,7 +143,7 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
     for (Candidate& c : cands) recoil_plan_free(c.plan);
   };
   size_t bulk = 0;
-  for (const recoil_batch_opts& o : candidates(keep)) {
+  for (const recoil_batch_opts& o : candidates(keep, any_adaptive(streams, count))) {
     Candidate c;
     c.opts = o;
     int rc = recoil_plan_create(streams, count, &c.opts, &c.plan);
