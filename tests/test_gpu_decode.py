@@ -398,3 +398,49 @@ def test_pipeline_cuts_a_large_stream_into_runs(recoil_lib, groups):
         assert pipe.errors() == 0
         for s, h in zip(want, host):
             assert np.array_equal(h.numpy().view(s.dtype), s)
+
+
+def test_batch_full_size_in_the_benchmark_launch_shape(recoil_lib):
+    """The 4096-stream uneven batch at full size (3.47 GB of symbols), decoded as the benchmark
+    times it: 8-warp CTAs, streams combined to 128 Ki-symbol splits, one persistent launch
+    replayed from a CUDA graph. Every stream against its input on the device, and a sample of
+    split threads against the oracle's split decoder on the same combined entries."""
+    from concurrent.futures import ThreadPoolExecutor
+    R = recoil_lib
+    specs = workloads.batch_specs()
+    syms = workloads.batch_symbols(specs)
+    with ThreadPoolExecutor(32) as ex:
+        streams = list(ex.map(lambda k: R.encode_with_splits(syms[k], 12, workloads.batch_split_count(len(syms[k]))),
+                              range(len(specs))))
+    opts = {"warps_per_cta": 8, "split_symbols": 131072, "flags": R.BATCH_GRAPH}
+    plan = R.Plan(streams, opts)
+    ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device="cuda")
+    outs = [torch.empty(max(1, len(s)), dtype=torch.uint8, device="cuda") for s in syms]
+    cs = torch.cuda.current_stream()
+    plan.upload(ws, stream=cs)
+    for _ in range(2):                                   # a replay writes the same bytes again
+        plan.decode([o.data_ptr() for o in outs], cs)
+    assert plan.errors(cs) == 0
+    for s, o in zip(syms, outs):
+        assert torch.equal(o[: len(s)], torch.from_numpy(s).cuda())
+    # sampled threads: the plan combines each stream to ceil(N / 128 Ki) splits rounded up to
+    # whole 8-warp CTAs; the oracle decodes the same entries thread by thread
+    rng = np.random.default_rng(11)
+    big = sorted(range(len(syms)), key=lambda k: -len(syms[k]))[:3]
+    for k in big + [int(v) for v in rng.choice(len(syms), size=3, replace=False)]:
+        s = syms[k]
+        want = -(-len(s) // 131072)
+        c = R.combine_splits(streams[k], -(-want // 8) * 8)
+        e = c.export()
+        K = c.info["n_entries"]
+        ost = oracle.OracleStream(len(s), 12, 32, 16, 16, e["freq"], e["words"], e["final"], None, None,
+                                  e["entry_word"].astype(np.int64),
+                                  np.vstack([e["entry_index"].astype(np.int64), np.zeros((1, 32), np.int64)]),
+                                  np.vstack([e["entry_state"].astype(np.uint32), e["final"][None, :]]))
+        got = outs[k][: len(s)].cpu().numpy()
+        for t in {0, K // 2, K - 1}:
+            lo, hi = oracle.owned_range(ost, t)
+            if hi < lo:
+                continue
+            ref = oracle.decode_thread(ost, t)
+            assert np.array_equal(got[lo:hi + 1], ref[lo:hi + 1].astype(np.uint8)), (k, t)
