@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--dist", default="zipf", choices=["zipf", "skewed", "uniform", "gauss16", "laplace"],
                     help="single: which stream (zipf 1 GiB, the 256 MiB extremes, laplace 1 MiB)")
     ap.add_argument("--splits", type=int, default=9472, help="zipf: decoder split count")
+    ap.add_argument("--alphabet", type=int, default=256, help="adaptive: symbols per PDF (up to 4096)")
+    ap.add_argument("--tables", type=int, default=64, help="adaptive: PDFs (table numbers drawn N(20, 12))")
     ap.add_argument("--sweep", type=lambda v: [int(x) for x in v.split(",") if x], default=[148, 592, 2368, 9472],
                     help="zipf: split counts to sweep (empty to skip)")
     ap.add_argument("--soak", type=float, default=1.0, help="seconds of untimed steps while sampling clocks")
@@ -423,7 +425,8 @@ def run_adaptive(a):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    st = workloads.adaptive_256mib(int((1 << 27) * a.scale))
+    st = workloads.adaptive_256mib(int((1 << 27) * a.scale), alphabet=a.alphabet, n_tables=a.tables)
+    default_model = a.alphabet == 256 and a.tables == 64
     tables = st.tables()
     s, tid = st.draw()
     enc = R.encode_adaptive(s, st.n_bits, tables, tid, max(1, min(65536, len(s) // 4096)))
@@ -504,17 +507,19 @@ def run_adaptive(a):
     line = {"metric": "decoded GB/s of an adaptive (per-symbol PDF) Recoil stream", "value": out_bytes / (mean_ms * 1e-3) / 1e9,
             "unit": "GB/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-            "config": {"workload": "adaptive: 2^27 uint16 latents, symbol i = clip(rint(128 + sigma_t Z)) with "
-                                   "t_i ~ clip(rint(N(20, 12)), 0, 63), 64 log-spaced Gaussian scale tables "
-                                   "(0.11..256) over 256 values, n=16, W=32",
+            "config": {"workload": f"adaptive: 2^27 uint16 latents, symbol i = clip(rint({a.alphabet // 2} + sigma_t Z)) "
+                                   f"with t_i ~ clip(rint(N(20, 12)), 0, {a.tables - 1}), {a.tables} log-spaced "
+                                   f"Gaussian scale tables (0.11..256) over {a.alphabet} values, n=16, W=32",
                        "splits": c.info["n_entries"], "warps_per_cta": warps, "autotuned": tuned,
                        "symbols_bytes": out_bytes,
                        "compressed_bytes": 2 * c.info["n_words"] + 4 * 32, "table_number_bytes": len(s),
                        "l2": "inputs larger than L2 (no flush)", "scale": a.scale},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                         "traffic": recorded_traffic(f"adaptive w{warps} k{a.splits}") if a.scale == 1.0 else None,
-                         "peak_source": peaks["source"], "kernel": "decode_kernel<kAdaptive16>",
+                         "traffic": (recorded_traffic(f"adaptive w{warps} k{a.splits}")
+                                     if a.scale == 1.0 and default_model else None),
+                         "peak_source": peaks["source"],
+                         "kernel": "decode_kernel<kAdaptive16>" if a.alphabet <= 256 else "decode_kernel<kAdaptive16Wide>",
                          "bytes": "compressed words + table numbers in, symbols out"},
             "clocks": clocks, "gpu_launches": launches * a.steps, "e2e": e2e, "split_sweep_gbs": sweep}
     if not a.no_cpu:

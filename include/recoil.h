@@ -120,7 +120,8 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target_splits, recoi
  *   n_tables     rows, 1..256; table_index holds n_syms bytes, each < n_tables
  *   alphabet     <= 4096 (256 for 8-bit symbols); the n_tables CDF rows must
  *                fit in shared memory with the decoder rings
- *                (n_tables * (alphabet + 1) * 2 bytes, rounded up, <= ~160 KiB)
+ *                (n_tables * (alphabet + 1) * 2 bytes, rounded up, <= ~160 KiB);
+ *                a plan adds a bucket guide per row where room is left
  * Split placement, combining and plans work as for static streams; adaptive
  * streams decode with 4, 8, 16 or 32 warps per CTA, are not serialised
  * (recoil_serialize) and not taken by recoil_decode_noalloc.

@@ -34,6 +34,8 @@
 // a fault or a hang.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "recoil_internal.h"
 
 namespace recoil {
@@ -90,44 +92,32 @@ struct Tables {
 // H(s) < slot for s >= 1; then F(s) = H(s) + 1 and f = H(s+1) - H(s), both
 // modulo 2^16 and exact since every f of an adaptive model is below 2^16.
 //
-// GUIDED (alphabets up to 256): the row's guide holds, for each of 2^g equal
-// buckets of slots, the symbol owning the bucket's first slot (one byte),
-// then the owner of the last slot; the symbol of `slot` lies between the
-// entries of its bucket and the next, and a binary search narrows that range
-// (usually empty: one lookup). Otherwise a 12-step binary search over the
-// whole row.
-template <bool GUIDED>
+// The row's guide holds, for each of 2^g equal buckets of slots, the symbol
+// owning the bucket's first slot (G: one byte for alphabets up to 256, else
+// two), then the owner of the last slot; the symbol of `slot` lies between
+// the entries of its bucket and the next, and a binary search narrows that
+// range (usually empty: one lookup; with g = 0 it is the whole row).
+template <typename G>
 struct AdaptiveTables {
   const uint16_t* cdf;
-  const uint8_t* guide;
-  uint32_t stride, gstride, gshift, A;
+  const G* guide;
+  uint32_t stride, gstride, gshift;
   __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream& st) {
     cdf = reinterpret_cast<const uint16_t*>(smem);
-    guide = smem + (size_t)st.n_tables * st.row_stride * 2;
+    guide = reinterpret_cast<const G*>(smem + (size_t)st.n_tables * st.row_stride * 2);
     stride = st.row_stride;
-    gstride = st.guide_stride;
+    gstride = st.guide_stride / sizeof(G);
     gshift = st.n_bits > st.guide_bits ? st.n_bits - st.guide_bits : 0;
-    A = st.alphabet;
   }
   __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask, uint32_t t) const {
     const uint32_t slot = x & mask;
     const uint16_t* row = cdf + t * stride;
-    uint32_t s;
-    if (GUIDED) {
-      const uint8_t* gb = guide + t * gstride + (slot >> gshift);
-      s = gb[0];
-      uint32_t hi = gb[1];
-      while (s < hi) {                                  // bounded: hi - s halves
-        const uint32_t mid = (s + hi + 1) >> 1;
-        if (row[mid] < slot) s = mid; else hi = mid - 1;
-      }
-    } else {
-      s = 0;
-#pragma unroll
-      for (int k = 11; k >= 0; --k) {
-        const uint32_t m = s | (1u << k);
-        if (m < A && row[m] < slot) s = m;
-      }
+    const G* gb = guide + t * gstride + (slot >> gshift);
+    uint32_t s = gb[0];
+    uint32_t hi = gb[1];
+    while (s < hi) {                                    // bounded: hi - s halves
+      const uint32_t mid = (s + hi + 1) >> 1;
+      if (row[mid] < slot) s = mid; else hi = mid - 1;
     }
     const uint32_t h0 = row[s];
     const uint32_t f = (row[s + 1] - h0) & 0xffffu;
@@ -148,7 +138,7 @@ struct TablesOf {
 };
 template <uint32_t KIND>
 struct TablesOf<KIND, true> {
-  using T = AdaptiveTables<adaptive_kind_guided(KIND)>;
+  using T = AdaptiveTables<typename std::conditional<adaptive_guide_entry_bytes(KIND) == 2, uint16_t, uint8_t>::type>;
 };
 
 template <uint32_t KIND>

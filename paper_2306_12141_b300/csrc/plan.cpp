@@ -42,22 +42,35 @@ uint32_t adaptive_row_stride(uint32_t A) {
 
 uint32_t guide_bits(uint32_t n, uint32_t g) { return std::min<uint32_t>(g, n); }
 
-// Bytes between guide rows: 2^g + 1 one-byte entries, an odd number of
+// Bytes between guide rows: 2^g + 1 entries of `eb` bytes, an odd number of
 // 32-bit words (rows start in different banks).
-uint32_t guide_stride(uint32_t n, uint32_t g) {
-  uint32_t words = ((1u << guide_bits(n, g)) + 1 + 3) / 4;
+uint32_t guide_stride(uint32_t n, uint32_t g, uint32_t eb) {
+  uint32_t words = (((1u << guide_bits(n, g)) + 1) * eb + 3) / 4;
   if (!(words & 1)) words++;
   return 4 * words;
 }
 
-// A guided adaptive stream's table image holds two variants, CDF rows then
-// a guide of 2^9 buckets per row, and the same rows with 2^10 buckets; a plan
-// stages one of them. Offset and size of variant g within the image:
-void guided_variant(const Stream& s, uint32_t g, size_t* off, size_t* bytes) {
+// An adaptive stream's table image holds three variants, each the CDF rows
+// followed by a guide row per PDF: 2^9 buckets, 2^10 buckets, one bucket; a
+// plan stages one of them. The guide widths in image order:
+constexpr uint32_t kGuideVariants[3] = {kGuideBits, kGuideBitsFine, kGuideBitsNone};
+
+// Offset and size of the variant with guide width g within the image.
+void guide_variant(const Stream& s, uint32_t g, size_t* off, size_t* bytes) {
   const size_t rows = (size_t)s.n_tables * adaptive_row_stride(s.alphabet()) * 2;
-  const size_t coarse = align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, kGuideBits), 16);
-  *off = g == kGuideBits ? 0 : coarse;
-  *bytes = g == kGuideBits ? coarse : align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, g), 16);
+  const uint32_t eb = adaptive_guide_entry_bytes(table_kind_of(s));
+  size_t o = 0;
+  for (uint32_t v : kGuideVariants) {
+    const size_t b = align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, v, eb), 16);
+    if (v == g) {
+      *off = o;
+      *bytes = b;
+      return;
+    }
+    o += b;
+  }
+  *off = 0;
+  *bytes = 0;
 }
 
 // Decoder tables of a stream (built once and cached on the stream).
@@ -69,39 +82,38 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
   if (s.table_img.empty()) {
     if (is_adaptive_kind(k)) {
       // one row per PDF: H(s) = F(s) - 1 modulo 2^16 for s = 0..A (H(0) = 0xffff,
-      // H(A) = 2^n - 1); guided kinds then add a guide row per PDF: for each of
-      // the 2^g buckets of slots the symbol owning its first slot, one byte,
-      // and after them the owner of the last slot, so that entries b and b + 1
-      // bracket the symbol of any slot in bucket b. Guided kinds hold the rows
-      // twice, once with each guide width (guided_variant).
+      // H(A) = 2^n - 1), then a guide row per PDF: for each of the 2^g buckets
+      // of slots the symbol owning its first slot, and after them the owner of
+      // the last slot, so that entries b and b + 1 bracket the symbol of any
+      // slot in bucket b. The image holds the rows once per guide width.
       const uint32_t stride = adaptive_row_stride(A);
       const size_t rows_bytes = (size_t)s.n_tables * stride * 2;
-      const bool guided = adaptive_kind_guided(k);
-      size_t off9 = 0, size9 = align_up(rows_bytes, 16), off10 = 0, size10 = 0;
-      if (guided) {
-        guided_variant(s, kGuideBits, &off9, &size9);
-        guided_variant(s, kGuideBitsFine, &off10, &size10);
+      const uint32_t eb = adaptive_guide_entry_bytes(k);
+      size_t total = 0, off = 0, bytes = 0;
+      for (uint32_t v : kGuideVariants) {
+        guide_variant(s, v, &off, &bytes);
+        total = off + bytes;
       }
-      s.table_img.assign(guided ? off10 + size10 : size9, 0);
+      s.table_img.assign(total, 0);
       std::vector<uint32_t> F(A + 1);
-      for (const size_t base : {off9, off10}) {
-        uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data() + base);
-        uint8_t* guide = s.table_img.data() + base + rows_bytes;
-        const uint32_t g = base == off9 ? kGuideBits : kGuideBitsFine;
-        const uint32_t gb = guide_bits(n, g), gstride = guide_stride(n, g);
+      for (uint32_t v : kGuideVariants) {
+        guide_variant(s, v, &off, &bytes);
+        uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data() + off);
+        uint8_t* guide = s.table_img.data() + off + rows_bytes;
+        const uint32_t gb = guide_bits(n, v), gstride = guide_stride(n, v, eb);
         for (uint32_t t = 0; t < s.n_tables; t++) {
           F[0] = 0;
           for (uint32_t sym = 0; sym < A; sym++) F[sym + 1] = F[sym] + s.freq[(size_t)t * A + sym];
           for (uint32_t sym = 0; sym <= A; sym++) cdf[(size_t)t * stride + sym] = (uint16_t)(F[sym] - 1);
-          if (!guided) continue;
           uint32_t sym = 0;
           for (uint32_t b = 0; b <= (1u << gb); b++) {
             const uint32_t slot = std::min<uint32_t>(b << (n - gb), (1u << n) - 1);
             while (F[sym + 1] <= slot) sym++;              // the symbol whose slots hold `slot`
-            guide[(size_t)t * gstride + b] = (uint8_t)sym;
+            uint8_t* e = guide + (size_t)t * gstride + (size_t)b * eb;
+            e[0] = (uint8_t)sym;
+            if (eb == 2) e[1] = (uint8_t)(sym >> 8);       // little-endian 16-bit entry
           }
         }
-        if (!guided) break;
       }
     } else if (k == kPacked8) {
       s.table_img.assign(align_up((size_t)slots * 4, 16), 0);
@@ -243,27 +255,33 @@ static uint64_t adaptive_ctas_per_sm(uint32_t warps, size_t smem) {
   return std::min<uint64_t>((uint64_t)per_sm / (smem + (size_t)reserved), 32 / warps);
 }
 
-// Guide width of each guided adaptive kind in a plan: the finer guide (about
-// a third fewer search steps on wide PDFs) unless its larger tables lower the
-// number of the kind's splits that the GPU decodes at once.
+// Guide width of each adaptive kind in a plan: 2^10 buckets (about a third
+// fewer search steps on wide PDFs than 2^9) unless those larger tables lower
+// the number of the kind's splits that the GPU decodes at once; else 2^9;
+// one bucket where not even the 2^9 guide fits beside the decoder rings.
 static void choose_guides(const recoil_plan* P, uint32_t* guide) {
   uint64_t entries[kKinds] = {};
   size_t coarse[kKinds] = {}, fine[kKinds] = {};
   for (uint32_t k = 0; k < kKinds; k++) guide[k] = kGuideBits;
   for (const Stream* s : P->streams) {
     const uint32_t k = table_kind_of(*s);
-    if (!adaptive_kind_guided(k)) continue;
+    if (!is_adaptive_kind(k)) continue;
     entries[k] += P->shard ? P->entry_last - P->entry_first : s->entries.size() + 1;
     size_t off = 0, bytes = 0;
-    guided_variant(*s, kGuideBits, &off, &bytes);
+    guide_variant(*s, kGuideBits, &off, &bytes);
     coarse[k] = std::max(coarse[k], bytes);
-    guided_variant(*s, kGuideBitsFine, &off, &bytes);
+    guide_variant(*s, kGuideBitsFine, &off, &bytes);
     fine[k] = std::max(fine[k], bytes);
   }
   const size_t rings = (size_t)P->warps * ring_smem_per_warp() + 16;
   const uint64_t sms = (uint64_t)device_sms();
   for (uint32_t k = 0; k < kKinds; k++) {
-    if (!entries[k] || fine[k] + rings > kMaxSmem) continue;
+    if (!entries[k]) continue;
+    if (coarse[k] + rings > kMaxSmem) {
+      guide[k] = kGuideBitsNone;
+      continue;
+    }
+    if (fine[k] + rings > kMaxSmem) continue;
     const uint64_t cap9 = adaptive_ctas_per_sm(P->warps, coarse[k] + rings) * sms * P->warps;
     const uint64_t cap10 = adaptive_ctas_per_sm(P->warps, fine[k] + rings) * sms * P->warps;
     if (std::min(entries[k], cap10) >= std::min(entries[k], cap9)) guide[k] = kGuideBitsFine;
@@ -354,14 +372,14 @@ static int plan_build(recoil_plan* P) {
       d.tid = (int64_t)word_off - (int64_t)(tlo / 2);
       d.row_stride = adaptive_row_stride(s.alphabet());
       d.n_tables = s.n_tables;
-      if (adaptive_kind_guided(kind)) {
+      {
         // stage the variant of the plan's guide width
         size_t voff = 0, vbytes = 0;
-        guided_variant(s, guide[kind], &voff, &vbytes);
+        guide_variant(s, guide[kind], &voff, &vbytes);
         d.table += voff;
         d.table_bytes = (uint32_t)vbytes;
         d.guide_bits = guide_bits(s.n_bits, guide[kind]);
-        d.guide_stride = guide_stride(s.n_bits, guide[kind]);
+        d.guide_stride = guide_stride(s.n_bits, guide[kind], adaptive_guide_entry_bytes(kind));
       }
       P->tid_off[i] = word_off;
       P->tid_lo[i] = tlo;

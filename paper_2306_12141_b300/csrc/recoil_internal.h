@@ -28,20 +28,23 @@ enum TableKind : uint32_t {
   kPacked8 = 0,    // 8-bit symbols, n <= 12, f < 4096: one u32 per slot = bias | sym << 12 | f << 20
   kGeneric8 = 1,   // 8-bit symbols otherwise: u16 slot -> symbol, u32 symbol -> (f-1) << 16 | F
   kGeneric16 = 2,  // 16-bit symbols: same tables as kGeneric8, 16-bit stores
-  // adaptive model (a PDF row per symbol index): one u16 CDF row per PDF
-  kAdaptive8 = 3,       // 8-bit symbols; a bucket guide per row narrows the search
-  kAdaptive16 = 4,      // 16-bit symbols, alphabet <= 256; bucket guide
-  kAdaptive16Wide = 5,  // 16-bit symbols, alphabet <= 4096; 12-step binary search
+  // adaptive model (a PDF row per symbol index): one u16 CDF row per PDF and
+  // a bucket guide per row that narrows the search
+  kAdaptive8 = 3,       // 8-bit symbols; one-byte guide entries
+  kAdaptive16 = 4,      // 16-bit symbols, alphabet <= 256; one-byte guide entries
+  kAdaptive16Wide = 5,  // 16-bit symbols, alphabet <= 4096; two-byte guide entries
   kKinds = 6,
 };
 
 __host__ __device__ constexpr bool is_adaptive_kind(uint32_t k) { return k >= kAdaptive8 && k < kKinds; }
-// Kinds whose rows come with a bucket guide (alphabets up to 256: one byte per bucket).
-__host__ __device__ constexpr bool adaptive_kind_guided(uint32_t k) { return k == kAdaptive8 || k == kAdaptive16; }
-// The guide of a row: 2^g buckets over the 2^n slots, g = min(9, n), or
-// min(10, n) where a plan can afford twice the guide's shared memory.
+// Bytes of a guide entry (a symbol number) of an adaptive kind.
+__host__ __device__ constexpr uint32_t adaptive_guide_entry_bytes(uint32_t k) { return k == kAdaptive16Wide ? 2 : 1; }
+// The guide of a row: 2^g buckets over the 2^n slots (at most 2^n). A plan
+// stages g = 9, or 10 where it can afford twice the guide's shared memory,
+// or 0 (one bucket: the whole row is searched) where even 9 does not fit.
 constexpr uint32_t kGuideBits = 9;
 constexpr uint32_t kGuideBitsFine = 10;
+constexpr uint32_t kGuideBitsNone = 0;
 
 // Longest alphabet of an adaptive model (the decoder's CDF search covers 2^12 symbols).
 constexpr uint32_t kMaxAdaptiveAlphabet = 4096;
@@ -111,11 +114,11 @@ struct alignas(16) DevStream {
   uint32_t table_bytes;      // bytes of the table image (multiple of 16)
   union {
     uint32_t slot_bytes;     // generic kinds: bytes of the slot -> symbol part (multiple of 16)
-    uint32_t guide_bits;     // guided adaptive kinds: log2 of the guide buckets per row
+    uint32_t guide_bits;     // adaptive kinds: log2 of the guide buckets per row
   };
   uint32_t row_stride;       // adaptive: 16-bit entries between CDF rows (odd number of 32-bit words)
   uint32_t n_tables;         // adaptive: CDF rows
-  uint32_t guide_stride;     // guided adaptive kinds: bytes between guide rows (after all CDF rows; 1 B per bucket boundary)
+  uint32_t guide_stride;     // adaptive kinds: bytes between guide rows (after all CDF rows; one entry per bucket boundary)
 };
 static_assert(sizeof(DevStream) == 64, "DevStream layout");
 

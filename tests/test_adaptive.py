@@ -149,6 +149,34 @@ def test_gpu_adaptive_cta_sizes_and_graph(recoil_lib, warps):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("warps", [8, 32])
+def test_gpu_adaptive_tables_too_large_for_a_guide(recoil_lib, warps):
+    """256 PDFs over 256 symbols at n = 16: the CDF rows take 132 KB, so no 2^9-bucket guide
+    fits beside them (another 132 KB); the plan stages the one-bucket guide and the decoder
+    searches whole rows."""
+    R = recoil_lib
+    a, tables, s, tid = _case(300_007, 23, n_bits=16, sym_bytes=2, n_tables=256, alphabet=256)
+    p = R.encode_adaptive(s, 16, tables, tid, 512)
+    (out,) = _gpu_decode(R, [p], {"warps_per_cta": warps})
+    assert np.array_equal(out, s)
+
+
+@pytest.mark.gpu
+def test_gpu_adaptive_wide_alphabet_guides(recoil_lib):
+    """4096-symbol alphabets take two-byte guide entries. 20 PDFs: 164 KB of CDF rows, with
+    a 2^9-bucket guide 184 KB, with 2^10 buckets 204 KB; 4-warp CTAs stage the finer guide,
+    16-warp CTAs (32 KB of rings) the coarser one. Each against the oracle's split decode."""
+    R = recoil_lib
+    a, tables, s, tid = _case(2_000_003, 24, n_bits=16, sym_bytes=2, n_tables=20, alphabet=4096)
+    p = R.encode_adaptive(s, 16, tables, tid, 4096)
+    o = oracle.encode_adaptive_with_splits(s, tid, tables, 16, 4096)
+    for Mp, w in ((64, 4), (4096, 16), (4096, 8)):
+        (out,) = _gpu_decode(R, [R.combine_splits(p, Mp)], {"warps_per_cta": w})
+        assert np.array_equal(out, s), (Mp, w)
+        assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(np.uint16)), (Mp, w)
+
+
+@pytest.mark.gpu
 def test_gpu_adaptive_mixed_batch(recoil_lib):
     """Adaptive streams of both symbol sizes next to static streams of every kind, one plan."""
     R = recoil_lib

@@ -324,9 +324,10 @@ class AdaptiveStream:
         return sym, tid
 
 
-def adaptive_256mib(n_syms: int = 1 << 27) -> AdaptiveStream:
-    """2^27 uint16 latents (256 MiB decoded), 64 Gaussian scale tables over 256 values, n = 16."""
-    return AdaptiveStream("adaptive", n_syms)
+def adaptive_256mib(n_syms: int = 1 << 27, alphabet: int = 256, n_tables: int = 64) -> AdaptiveStream:
+    """2^27 uint16 latents (256 MiB decoded), 64 Gaussian scale tables over 256 values, n = 16
+    (other alphabets and table counts for the wide-alphabet variant)."""
+    return AdaptiveStream("adaptive", n_syms, alphabet=alphabet, n_tables=n_tables)
 
 
 def poisson_arrivals(rate_hz: float, count: int, seed: int = 7) -> np.ndarray:
