@@ -56,6 +56,17 @@ bool Stream::constant() const {
   return false;
 }
 
+const std::vector<uint32_t>& Stream::owned_ends() const {
+  std::lock_guard<std::mutex> g(cache_mu);
+  if (!owned_end_ready) {
+    owned_end.resize(entries.size());
+    for (size_t e = 0; e < entries.size(); e++)
+      owned_end[e] = *std::min_element(entries[e].idx, entries[e].idx + kW);
+    owned_end_ready = true;
+  }
+  return owned_end;
+}
+
 // --------------------------------------------------------------- quantiser
 // Present symbols get max(1, round_half_even(c 2^n / N)); then the sum is
 // corrected to 2^n one unit at a time, cycling over present symbols in order
@@ -402,8 +413,7 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_strea
     // decrease, so each choice is a binary search.
     const uint64_t R = in->entries.size();                    // regular entries
     const uint64_t Mp = std::min<uint64_t>(target, R + 1);
-    std::vector<uint64_t> m(R);
-    for (uint64_t e = 0; e < R; e++) m[e] = *std::min_element(in->entries[e].idx, in->entries[e].idx + kW);
+    const std::vector<uint32_t>& m = in->owned_ends();       // cached: serving combines per request
     uint64_t first = 0;
     for (uint64_t k = 0; k + 1 < Mp; k++) {
       const uint64_t last = R - (Mp - 1 - k);
@@ -416,11 +426,13 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_strea
       } else {
         const uint64_t a = m[b - 1];                                // the largest end below t
         if (b <= last && m[b] - t < t - a) pick = b;
-        else pick = std::lower_bound(lo, m.begin() + b, a) - m.begin();
+        else pick = std::lower_bound(lo, m.begin() + b, (uint32_t)a) - m.begin();
       }
       s->entries.push_back(in->entries[pick]);
+      s->owned_end.push_back(m[pick]);
       first = pick + 1;
     }
+    s->owned_end_ready = true;
     *out = s.release();
     return RECOIL_OK;
   } catch (const std::bad_alloc&) {

@@ -78,12 +78,15 @@ struct Stream {
   mutable std::mutex cache_mu;
   mutable std::vector<uint8_t> table_img;          // decoder tables, padded to 16 B
   mutable uint32_t table_kind = 0;
+  mutable std::vector<uint32_t> owned_end;         // per regular entry: its smallest recorded index
+  mutable bool owned_end_ready = false;
 
   uint64_t n_words() const { return words ? words->size() : 0; }
   const uint16_t* word_data() const { return pinned_words ? pinned_words.get() : (words ? words->data() : nullptr); }
   uint32_t alphabet() const { return (uint32_t)(n_tables ? freq.size() / n_tables : freq.size()); }
   bool adaptive() const { return n_tables != 0; }
   bool constant() const;                           // a single symbol owns all 2^n slots (static model)
+  const std::vector<uint32_t>& owned_ends() const; // owned_end, built on first use (entries never change)
 };
 
 // ------------------------------------------------------------ device images
