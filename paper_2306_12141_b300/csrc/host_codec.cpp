@@ -307,7 +307,9 @@ static int encode_common(const void* syms, uint64_t n_syms, const recoil_params*
       // below the first one recorded for a symbol >= m
       const uint32_t m = *std::min_element(e.idx, e.idx + kW);
       e.wlo = (uint64_t)(std::lower_bound(rec.sym.begin(), rec.sym.end(), m) - rec.sym.begin());
+      s->owned_end.push_back(m);
     }
+    s->owned_end_ready = true;
     s->words = words;
     *out = s.release();
     return RECOIL_OK;
@@ -414,12 +416,21 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_strea
     const uint64_t R = in->entries.size();                    // regular entries
     const uint64_t Mp = std::min<uint64_t>(target, R + 1);
     const std::vector<uint32_t>& m = in->owned_ends();       // cached: serving combines per request
+    s->entries.reserve(Mp - 1);
+    s->owned_end.reserve(Mp - 1);
     uint64_t first = 0;
     for (uint64_t k = 0; k + 1 < Mp; k++) {
       const uint64_t last = R - (Mp - 1 - k);
       const uint64_t t = (uint64_t)((unsigned __int128)(k + 1) * in->n_syms / Mp);
-      const auto lo = m.begin() + first, hi = m.begin() + last + 1;
-      const uint64_t b = std::lower_bound(lo, hi, t) - m.begin();  // first end >= t
+      // the first end >= t in [first, last]: gallop from the previous pick
+      // (targets are about R / Mp entries apart), then bisect the last stride
+      uint64_t below = first, step = 1;
+      while (below + step <= last && m[below + step - 1] < t) {
+        below += step;
+        step *= 2;
+      }
+      const auto lo = m.begin() + first;
+      const uint64_t b = std::lower_bound(m.begin() + below, m.begin() + std::min(below + step, last + 1), t) - m.begin();
       uint64_t pick;
       if (b == first) {
         pick = b;
@@ -529,7 +540,9 @@ int recoil_stream_import(const recoil_params* params, uint64_t n_syms, uint32_t 
       (void)mx;
       prev_word = e.word;
       prev_min = mn;
+      s->owned_end.push_back(mn);
     }
+    s->owned_end_ready = true;
     *out = s.release();
     return RECOIL_OK;
   } catch (const std::bad_alloc&) {
