@@ -142,7 +142,7 @@ def recorded_traffic(key: str):
     try:
         text = open(path).read()
         h = hashlib.sha256()
-        for f in ("decode_kernels.cu", "recoil_internal.h"):
+        for f in ("decode_kernels.cu", "device_types.h"):
             h.update(open(os.path.join(src, f), "rb").read())
     except OSError:
         return None

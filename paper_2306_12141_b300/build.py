@@ -8,7 +8,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librecoil.so")
 SOURCES = ["decode_kernels.cu", "plan.cpp", "host_codec.cpp", "tune.cpp", "serve.cpp", "pipeline.cpp", "serialize.cpp", "noalloc.cu"]
-HEADERS = ["recoil_internal.h"]
+HEADERS = ["recoil_internal.h", "device_types.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -36,7 +36,7 @@
 
 #include <type_traits>
 
-#include "recoil_internal.h"
+#include "device_types.h"
 
 namespace recoil {
 namespace {
