@@ -104,6 +104,20 @@ def test_adaptive_rejected_by_noalloc_and_small_ctas(recoil_lib):
             R.Plan([p], {"warps_per_cta": w})
 
 
+def test_adaptive_plan_rejects_rows_beyond_shared_memory(recoil_lib):
+    """256 PDFs over 1000 symbols need 513 KB of CDF rows: the plan refuses them with an
+    error (no guide width makes them fit), while 64 such PDFs (128 KB) plan."""
+    R = recoil_lib
+    for T, ok in ((256, False), (64, True)):
+        a, tables, s, tid = _case(20_000, 25, n_bits=16, sym_bytes=2, n_tables=T, alphabet=1000)
+        p = R.encode_adaptive(s, 16, tables, tid, 8)
+        if ok:
+            assert R.Plan([p], {"warps_per_cta": 8}).workspace_size > 0
+        else:
+            with pytest.raises(R.RecoilError):
+                R.Plan([p], {"warps_per_cta": 8})
+
+
 # ------------------------------------------------------------------- GPU
 def _gpu_decode(R, streams, opts=None):
     import torch
