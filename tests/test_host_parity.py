@@ -77,6 +77,22 @@ def test_combine_matches_oracle_rule(recoil_lib, K, Mp):
     assert np.array_equal(ec["words"], ep["words"])
 
 
+def test_combine_matches_oracle_rule_on_uneven_splits(recoil_lib):
+    """A skewed source: encoded split sizes drift along the stream and many entries share an
+    owned end, so the nearest-end choice, its ties and the window that leaves room for later
+    targets all matter; every target count from 1 to K agrees with the oracle."""
+    s = workloads.Stream("sk", 1 << 18, 1, 12, "skewed", {"p0": 0.95}, seed=8).symbols()
+    p = recoil_lib.encode_with_splits(s, 12, 96)
+    ep = p.export()
+    K = p.info["n_entries"]
+    ends = ep["entry_index"].astype(np.int64).min(axis=1)
+    for Mp in range(1, K + 2):
+        c = recoil_lib.combine_splits(p, Mp)
+        keep = oracle.combine_keep(ends, len(s), Mp)
+        regular = [k for k in keep if k < K - 1]
+        assert np.array_equal(c.export()["entry_word"], ep["entry_word"][regular]), Mp
+
+
 def test_import_round_trip_and_validation(recoil_lib):
     R = recoil_lib
     st = workloads.laplace_1mib(1 << 16)
