@@ -134,8 +134,9 @@ def aggregate(ms_local: float, bytes_local: int, device=None):
     return float(t.item()), int(b.item())
 
 
-def recorded_traffic(key: str):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel sources still match it."""
+def recorded_traffic(key: str, what: str = "traffic_bytes"):
+    """A per-launch count recorded by an ncu capture (DRAM bytes, or warp instructions with
+    what="instructions"), if the kernel sources still match the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "decode_kernel_traffic.md")
     src = os.path.join(ROOT, "paper_2306_12141_b300", "csrc")
@@ -151,9 +152,27 @@ def recorded_traffic(key: str):
         return None
     for line in text.splitlines():
         line = line.strip()
-        if line.startswith(f"traffic_bytes {key}:"):
+        if line.startswith(f"{what} {key}:"):
             return int(line.split(":")[1])
     return None
+
+
+def issue_rate(key: str, mean_ms: float, dev, clocks: dict):
+    """The decode launch against the SMs' instruction-issue rate: warp instructions per launch
+    (ncu, recorded with the traffic) over the launch time measured here, against one warp
+    instruction per clock on each of 4 schedulers of every SM at the sampled SM clock. The
+    kernel is bound by integer issue long before HBM, so this is the fraction that says how
+    close it runs to its own limit; None without a matching record."""
+    import torch
+    inst = recorded_traffic(key, "instructions")
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if inst is None or not mhz:
+        return None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    achieved = inst / (mean_ms * 1e-3)
+    peak = sms * 4 * mhz * 1e6
+    return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s", "frac": achieved / peak,
+            "instructions_per_launch": inst, "peak_from": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (sampled)"}
 
 
 def kernel_of(info: dict) -> tuple[str, str]:
@@ -518,6 +537,8 @@ def run_adaptive(a):
                          "frac": achieved / peaks["hbm_gbs"], "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                          "traffic": (recorded_traffic(f"adaptive w{warps} k{a.splits}")
                                      if a.scale == 1.0 and default_model else None),
+                         "issue": (issue_rate(f"adaptive w{warps} k{a.splits}", mean_ms, dev, clocks)
+                                   if a.scale == 1.0 and default_model else None),
                          "peak_source": peaks["source"],
                          "kernel": "decode_kernel<kAdaptive16>" if a.alphabet <= 256 else "decode_kernel<kAdaptive16Wide>",
                          "bytes": "compressed words + table numbers in, symbols out"},
@@ -715,6 +736,8 @@ def run_ours(a):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"],
                      "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                     "issue": (issue_rate(tkey, mean_ms, dev, clocks)
+                               if a.scale == 1.0 and a.streams == workloads.BATCH_STREAMS else None),
                      "kernel": kernel, "bytes": "compressed words in + symbols out"},
         "clocks": clocks,
         "gpu_launches": launches * a.steps,
