@@ -134,6 +134,15 @@ def aggregate(ms_local: float, bytes_local: int, device=None):
     return float(t.item()), int(b.item())
 
 
+def code_only(source: str) -> str:
+    """C++/CUDA source without comments and blank runs, so that the recorded counts stay tied to
+    what compiles, not to how it is annotated."""
+    import re
+    source = re.sub(r"/\*.*?\*/", " ", source, flags=re.S)
+    source = re.sub(r"//[^\n]*", "", source)
+    return "\n".join(line.rstrip() for line in source.splitlines() if line.strip())
+
+
 def recorded_traffic(key: str, what: str = "traffic_bytes"):
     """A per-launch count recorded by an ncu capture (DRAM bytes, or warp instructions with
     what="instructions"), if the kernel sources still match the capture."""
@@ -144,7 +153,7 @@ def recorded_traffic(key: str, what: str = "traffic_bytes"):
         text = open(path).read()
         h = hashlib.sha256()
         for f in ("decode_kernels.cu", "device_types.h"):
-            h.update(open(os.path.join(src, f), "rb").read())
+            h.update(code_only(open(os.path.join(src, f)).read()).encode())
     except OSError:
         return None
     want = f"kernel_sources_sha256_16: {h.hexdigest()[:16]}"

@@ -16,7 +16,8 @@
 //
 // Memory: decoder tables are staged in shared memory once per work item
 // (Sec. 4.4 packs symbol, f and F into one 32-bit entry for 8-bit symbols and
-// n <= 12; adaptive models stage one CDF row per PDF, Sec. 3.1); the
+// n <= 12; adaptive models stage one CDF row and one bucket guide per PDF,
+// Sec. 3.1); the
 // compressed words a warp is about to consume sit in a per-warp shared ring
 // refilled 512 bytes at a time with one 16-byte load per lane, issued a chunk
 // ahead so that the dependent renormalisation reads never wait on HBM.
