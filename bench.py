@@ -714,9 +714,12 @@ def run_ours(a):
                                                                                 s.view(np.uint8)))
             assert bad == 0, f"{bad} streams wrong end to end"
             h2d = sum(2 * st.info["n_words"] for st in streams)
-            e2e = {"value": world * out_bytes / (statistics.mean(e_ms) * 1e-3) / 1e9, "unit": "GB/s",
-                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_bytes),
-                   "ms_per_step": statistics.mean(e_ms), "groups": a.e2e_groups,
+            # whole job: the slowest rank's time, every rank's bytes (collectives on all ranks)
+            e_job_ms, e_job_bytes = aggregate(statistics.mean(e_ms), out_bytes, dev if dist else None)
+            _, h2d_job = aggregate(statistics.mean(e_ms), h2d, dev if dist else None)
+            e2e = {"value": e_job_bytes / (e_job_ms * 1e-3) / 1e9, "unit": "GB/s",
+                   "h2d_bytes_per_step": int(h2d_job), "d2h_bytes_per_step": int(e_job_bytes),
+                   "ms_per_step": e_job_ms, "groups": a.e2e_groups,
                    "note": "recoil_pipeline_run: H2D of words (+ descriptors, tables), decode, D2H of the symbols, "
                            "overlapped across stream groups (a stream larger than its share is cut into runs "
                            "of splits)"}
