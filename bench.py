@@ -752,7 +752,7 @@ def run_ours(a):
                                if a.scale == 1.0 and a.streams == workloads.BATCH_STREAMS else None),
                      "kernel": kernel, "bytes": "compressed words in + symbols out"},
         "clocks": clocks,
-        "gpu_launches": launches * a.steps,
+        "gpu_launches": launches * a.steps * world,          # every rank's launches in the timed steps
         "e2e": e2e,
     }
     line.update(extra)
