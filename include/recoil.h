@@ -470,14 +470,14 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
  *   d_out        n_syms * sym_bytes bytes for the symbols
  * The split descriptors, decoder tables, work-queue counters and error flags
  * go to one static device array of RECOIL_NOALLOC_SCRATCH_BYTES that every GPU
- * loading the library holds until exit. The first call on a device looks up
- * that array's device address (with that device current), so make it before
- * any stream capture. Every call shares the array and finds the previous
+ * loading the library holds until exit; each call looks up its device address
+ * on the current device. Every call shares the array and finds the previous
  * call's contents there; a call clears the counters and flags it needs, but
  * calls whose GPU work overlaps (several host threads or CUDA streams) race on
  * it and must not be made. Allocates nothing on the device (host memory only
- * for building the descriptors). Returns after the decode has finished on
- * cuda_stream. Errors: EINVAL (null, small or misaligned d_words, an adaptive
+ * for building the descriptors). Synchronous: it copies the descriptors from
+ * host memory, waits on cuda_stream and returns after the decode has finished
+ * (also on an error return, nothing it queued is still running). Errors: EINVAL (null, small or misaligned d_words, an adaptive
  * stream, or a stream whose descriptors and tables exceed the array: combine
  * it to fewer splits),
  * ECORRUPT (the decoder found an inconsistent stream), ECUDA.

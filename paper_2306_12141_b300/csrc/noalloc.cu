@@ -17,7 +17,6 @@
 // work overlaps (from several host threads or on several CUDA streams) race
 // on the array and must not be issued.
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "recoil_internal.h"
@@ -26,31 +25,20 @@ namespace recoil {
 namespace {
 
 constexpr size_t kScratchBytes = RECOIL_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 // The decoder's per-call device data. In host code this name is only a host
 // stand-in for the symbol: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once per
-// device (with that device current) on the first call there.
+// Device address of the scratch array on the current device. Looked up on
+// every call (a host-side lookup): after a device reset the module is loaded
+// again and the array may sit elsewhere, so no address is kept between calls.
 int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(RECOIL_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(RECOIL_EINVAL, "device index out of range");
-  std::lock_guard<std::mutex> g(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(RECOIL_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(RECOIL_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = p;
   return RECOIL_OK;
 }
 
@@ -95,6 +83,24 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
   }
   uint8_t* scratch = static_cast<uint8_t*>(base);
   cudaStream_t cs = (cudaStream_t)cuda_stream;
+  int sms = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    recoil_plan_free(plan);
+    return fail(RECOIL_ECUDA, std::string("recoil_decode_noalloc: ") + cudaGetErrorString(e));
+  }
+  // every occupancy query before anything is enqueued, so that no error
+  // return leaves work queued on cuda_stream
+  int per_sm[kKinds] = {};
+  for (uint32_t k = 0; k < kKinds; k++) {
+    if (!img.kind_count[k]) continue;
+    const uint32_t smem = (uint32_t)((img.kind_smem[k] + 15) / 16 * 16);
+    if (occupancy_ctas_per_sm(k, img.warps, smem, &per_sm[k]) != 0 || per_sm[k] <= 0) {
+      recoil_plan_free(plan);
+      return fail(RECOIL_ECUDA, "occupancy query failed");
+    }
+  }
 
   // Host copy of the descriptors with the output pointer filled in; the
   // control block at its start is zero, which clears the previous call's
@@ -102,12 +108,9 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
   std::vector<uint8_t> meta(img.meta, img.meta + img.meta_bytes);
   void* outp = d_out;
   std::memcpy(meta.data() + img.off_outs, &outp, sizeof outp);
-  cudaError_t e = cudaMemcpyAsync(scratch, meta.data(), meta.size(), cudaMemcpyHostToDevice, cs);
+  e = cudaMemcpyAsync(scratch, meta.data(), meta.size(), cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess && img.table_bytes)
     e = cudaMemcpyAsync(scratch + off_tables, img.tables, img.table_bytes, cudaMemcpyHostToDevice, cs);
-  int sms = 0, dev = 0;
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
   LaunchArgs a{};
   a.streams = reinterpret_cast<const DevStream*>(scratch + img.off_streams);
@@ -126,17 +129,14 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
     a.persistent = 1;
     a.table_smem = (uint32_t)((img.kind_smem[k] + 15) / 16 * 16);
     a.warp_queue = img.kind_warp_queue[k];
-    int per_sm = 0;
-    if (occupancy_ctas_per_sm(k, img.warps, a.table_smem, &per_sm) != 0 || per_sm <= 0) {
-      recoil_plan_free(plan);
-      return fail(RECOIL_ECUDA, "occupancy query failed");
-    }
-    e = launch_decode(k, a, launch_grid(a, per_sm, sms), cs);
+    e = launch_decode(k, a, launch_grid(a, per_sm[k], sms), cs);
   }
   // read the error flags back (this also makes the call return after the decode)
   DevControl ctl;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, scratch, sizeof ctl, cudaMemcpyDeviceToHost, cs);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  // whatever failed above, nothing the call queued may still run once it returns
+  const cudaError_t es = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess) e = es;
   recoil_plan_free(plan);
   if (e != cudaSuccess) return fail(RECOIL_ECUDA, std::string("recoil_decode_noalloc: ") + cudaGetErrorString(e));
   if (ctl.errors)
