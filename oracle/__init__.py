@@ -11,9 +11,11 @@ it. It shares no code with the CUDA library and imports nothing from it.
 Every function here is pinned by ``tests/test_oracle_*.py`` against facts the
 paper or the mathematics fixes (lossless round trip, brute force over tiny
 alphabets, the Sec. 4.1 walkthrough, closed forms, entropy bounds, the
-paper's Table 4 sizes). The quantiser and the heuristic are readings of the
-paper, not the paper's own code: their exact outputs are "parity unpinned"
-against the paper and pinned only by their invariants.
+paper's Table 4 sizes). The quantiser is a reading of the paper, which gives
+no procedure: its exact output is "parity unpinned" against the paper and
+pinned only by hand cases and invariants. The heuristic comes in the printed
+form (T = ceil(N/M)) and in the remaining-symbols reading of T; both are pinned
+by hand-derived split words and the exhaustive argmin of Eq. 7.
 """
 from __future__ import annotations
 
@@ -60,8 +62,9 @@ def lib():
         L.oracle_encode.restype = i64
         L.oracle_decode_serial.argtypes = [p, i64, p, i64, p, i32, i32, i32, i32, i32, p, p, p, p, p]
         L.oracle_scan.argtypes = [p, p, i64, i32, p, p, p]
-        L.oracle_heuristic.argtypes = [p, p, i64, i64, i32, i64, p]
-        L.oracle_heuristic.restype = i64
+        for name in ("oracle_heuristic_eq7", "oracle_heuristic_remaining"):
+            getattr(L, name).argtypes = [p, p, i64, i64, i32, i64, p]
+            getattr(L, name).restype = i64
         L.oracle_combine.argtypes = [i64, i64, p, i64, p]
         L.oracle_combine.restype = i64
         L.oracle_decode_thread.argtypes = [p, i64, p, i64, p, i32, i32, i32, i32, i32,
@@ -189,12 +192,21 @@ def scan(ev_sym, ev_y, q: int, W: int = W_DEFAULT):
     return bool(ok), idx, y, wp
 
 
-def heuristic(ev_sym, ev_y, N: int, M: int, W: int = W_DEFAULT) -> np.ndarray:
-    """Split words chosen by Def. 4.1 / Eq. 7 for M splits (at most M-1 words)."""
+RULES = ("remaining", "eq7")
+
+
+def heuristic(ev_sym, ev_y, N: int, M: int, W: int = W_DEFAULT, rule: str = "remaining") -> np.ndarray:
+    """Split words chosen by Def. 4.1 / Eq. 7 for M splits (at most M-1 words).
+
+    rule "eq7": T = ceil(N / M) for every split, as printed; rule "remaining":
+    T = ceil((N - lo) / (M - k)) over the symbols left (the library's default)."""
+    if rule not in RULES:
+        raise ValueError(f"rule must be one of {RULES}")
+    fn = lib().oracle_heuristic_eq7 if rule == "eq7" else lib().oracle_heuristic_remaining
     q = np.zeros(max(1, M), dtype=np.int64)
-    k = lib().oracle_heuristic(_ptr(_i64(ev_sym)), _ptr(_u32(ev_y)), len(ev_sym), N, W, M, _ptr(q))
+    k = fn(_ptr(_i64(ev_sym)), _ptr(_u32(ev_y)), len(ev_sym), N, W, M, _ptr(q))
     if k < 0:
-        raise ValueError("oracle_heuristic failed")
+        raise ValueError("oracle heuristic failed")
     return q[:k].copy()
 
 
@@ -246,26 +258,26 @@ def entries_for(ev_sym, ev_y, qs, W: int):
 
 
 def encode_with_splits(sym, n: int, M: int, W: int = W_DEFAULT, lgL: int = LGL_DEFAULT,
-                       b: int = B_DEFAULT, alphabet: int | None = None) -> OracleStream:
-    """Quantise from the symbol counts, encode, and place M splits by the heuristic."""
+                       b: int = B_DEFAULT, alphabet: int | None = None, rule: str = "remaining") -> OracleStream:
+    """Quantise from the symbol counts, encode, and place M splits by the heuristic (`rule`: T of Eq. 7)."""
     s = _u32(sym)
     A = alphabet if alphabet is not None else (int(s.max()) + 1 if len(s) else 1)
     counts = np.bincount(s, minlength=A).astype(np.uint64)
     f = quantize(counts, n)
     words, final, ev_sym, ev_y = encode(s, f, n, W, lgL, b)
-    qs = heuristic(ev_sym, ev_y, len(s), M, W)
+    qs = heuristic(ev_sym, ev_y, len(s), M, W, rule)
     idx, y = entries_for(ev_sym, ev_y, qs, W)
     y[-1] = final
     return OracleStream(len(s), n, W, lgL, b, f, words, final, ev_sym, ev_y, qs, idx, y)
 
 
 def encode_adaptive_with_splits(sym, tid, tables, n: int, M: int, W: int = W_DEFAULT,
-                                lgL: int = LGL_DEFAULT, b: int = B_DEFAULT) -> OracleStream:
+                                lgL: int = LGL_DEFAULT, b: int = B_DEFAULT, rule: str = "remaining") -> OracleStream:
     """Adaptive encode (PDF row tid[i] for symbol i) and M splits placed by the heuristic."""
     s = _u32(sym)
     tab = np.ascontiguousarray(np.atleast_2d(tables), dtype=np.uint32)
     words, final, ev_sym, ev_y = encode_adaptive(s, tid, tab, n, W, lgL, b)
-    qs = heuristic(ev_sym, ev_y, len(s), M, W)
+    qs = heuristic(ev_sym, ev_y, len(s), M, W, rule)
     idx, y = entries_for(ev_sym, ev_y, qs, W)
     y[-1] = final
     return OracleStream(len(s), n, W, lgL, b, tab, words, final, ev_sym, ev_y, qs, idx, y, _u32(tid))

@@ -24,11 +24,14 @@
  *   - adaptive coding ............. Sec. 3.1 (the PDF of every coding step is chosen
  *                                   by the symbol index; here one row of a table set)
  *
- * Parity unpinned against the paper: the quantiser's and the heuristic's exact
- * outputs (the paper gives neither procedure in enough detail to reproduce its
- * numbers); they are pinned by hand cases, invariants and the exhaustive
- * argmin of Eq. 7 instead. Every other function is pinned to the paper or to
- * the mathematics by the oracle tests.
+ * Parity unpinned against the paper: the quantiser's exact output (the paper
+ * gives no procedure detailed enough to reproduce its numbers); it is pinned
+ * by hand cases and invariants instead. The heuristic as printed (T = ceil(N/M),
+ * oracle_heuristic_eq7) is pinned by a split word derived by hand and the
+ * exhaustive argmin of Eq. 7; the remaining-symbols reading of T
+ * (oracle_heuristic_remaining) by hand cases where the two differ and the same
+ * argmin. Every other function is pinned to the paper or to the mathematics by
+ * the oracle tests.
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   - Quantiser: f[s] = max(1, round_half_even(c[s] 2^n / N)) for present
@@ -361,24 +364,29 @@ static int64_t iabs(int64_t v) { return v < 0 ? -v : v; }
  * Split heuristic (Def. 4.1, Eq. 7). Chooses up to M-1 split words q[0..) in
  * increasing order; the final states make the M-th split. For split k, with
  * lo = the previous split's smallest recorded index (0 for the first),
- * t = top + 1 - lo and t_s = top + 1 - m, the word minimising
+ * t = top + 1 - lo symbols from the previous split point to this one
+ * (synchronisation section included) and t_s = top + 1 - m symbols in this
+ * split's synchronisation section, the word minimising
  * H = |t - T| + |t - t_s - T| is taken (ties: smaller word). T is the
- * expected number of symbols per split, taken over what is left:
- * T = ceil((N - lo) / (M - k)), which is ceil(N / M) for the first split.
- * (With ceil(N / M) throughout, each split falls short of T by about half
- * its synchronisation section and the shortfall piles up in the final split.)
- * The scan for one split stops once m - lo - T exceeds the best H so far,
- * since m never decreases with the word offset. Returns the number of split
- * words written to q_out (at most M-1).
+ * expected number of symbols per split:
+ *   remaining = 0: T = ceil(N / M) for every split, as Def. 4.1 prints it;
+ *   remaining = 1: T = ceil((N - lo) / (M - k)), T over what is left, which
+ *                  is ceil(N / M) for the first split (the reading the library
+ *                  uses by default: with the printed T each split falls short
+ *                  of T by about half its synchronisation section and the
+ *                  shortfall piles up in the final split).
+ * The scan for one split stops once m - lo - T exceeds the best H so far: H is
+ * at least |t - t_s - T| = |m - lo - T| and m never decreases with the word
+ * offset. Returns the number of split words written to q_out (at most M-1).
  */
-int64_t oracle_heuristic(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw, int64_t N,
-                         int W, int64_t M, int64_t *q_out) {
+static int64_t heuristic_eq7(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw, int64_t N,
+                             int W, int64_t M, int remaining, int64_t *q_out) {
     if (M < 1 || W < 1 || W > 64) return OR_EINVAL;
     int64_t idx[64], wp[64];
     uint32_t y[64];
     int64_t count = 0, lo = 0, qprev = -1;
     while (count < M - 1) {
-        int64_t T = (N - lo + (M - count) - 1) / (M - count);
+        int64_t T = remaining ? (N - lo + (M - count) - 1) / (M - count) : (N + M - 1) / M;
         int64_t best = -1, bestH = 0, best_m = 0;
         for (int64_t q = qprev + 1; q < nw; q++) {
             if (!oracle_scan(ev_sym, ev_y, q, W, idx, y, wp)) continue;
@@ -394,6 +402,18 @@ int64_t oracle_heuristic(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw
         qprev = best;
     }
     return count;
+}
+
+/* Def. 4.1 as printed: T = ceil(N / M) for every split. */
+int64_t oracle_heuristic_eq7(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw, int64_t N,
+                             int W, int64_t M, int64_t *q_out) {
+    return heuristic_eq7(ev_sym, ev_y, nw, N, W, M, 0, q_out);
+}
+
+/* Def. 4.1 with T over the symbols that remain, T = ceil((N - lo) / (M - k)). */
+int64_t oracle_heuristic_remaining(const int64_t *ev_sym, const uint32_t *ev_y, int64_t nw, int64_t N,
+                                   int W, int64_t M, int64_t *q_out) {
+    return heuristic_eq7(ev_sym, ev_y, nw, N, W, M, 1, q_out);
 }
 
 /*

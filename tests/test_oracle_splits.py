@@ -109,14 +109,18 @@ def _H(top, m, lo, T):
     return abs(t - T) + abs(t - ts - T)
 
 
+@pytest.mark.parametrize("rule", ["eq7", "remaining"])
 @pytest.mark.parametrize("dist,params,n,M", [
     ("laplace", dict(mean=128.0, scale=8.0), 11, 16),
     ("zipf", dict(s=1.2), 12, 9),
     ("skewed", dict(p0=0.95), 12, 5),
 ])
-def test_heuristic_attains_minimum_of_eq7(dist, params, n, M):
+def test_heuristic_attains_minimum_of_eq7(dist, params, n, M, rule):
+    """Every split word is the first usable word after the previous one that minimises
+    Eq. 7, over all usable words (no early stop); T = ceil(N/M) as printed ("eq7") or
+    over the symbols left ("remaining")."""
     s = workloads.Stream("t", 12000, 1, n, dist, params, seed=3).symbols()
-    st = oracle.encode_with_splits(s, n, M)
+    st = oracle.encode_with_splits(s, n, M, rule=rule)
     lo, qprev = 0, -1
     cand = []
     for q in range(len(st.words)):
@@ -124,7 +128,7 @@ def test_heuristic_attains_minimum_of_eq7(dist, params, n, M):
         if ok:
             cand.append((q, int(idx.max()), int(idx.min())))
     for k, q in enumerate(st.q):
-        T = -(-(st.N - lo) // (M - k))                 # expected symbols per remaining split
+        T = -(-st.N // M) if rule == "eq7" else -(-(st.N - lo) // (M - k))
         rest = [(c, _H(top, m, lo, T)) for c, top, m in cand if c > qprev]
         best = min(h for _, h in rest)
         first = min(c for c, h in rest if h == best)
@@ -132,6 +136,74 @@ def test_heuristic_attains_minimum_of_eq7(dist, params, n, M):
         lo = int(st.idx[k].min())
         qprev = q
     assert st.K <= M
+
+
+def _digit_stream(N):
+    """One coder (W = 1), n = 8, every f = 1, L = 2^16, b = 16: each symbol is a base-256
+    digit of the state, so a word leaves every second symbol. Worked by hand from
+    Eqs. 1 and 3: from x = 2^16, coding a symbol gives 2^24 + s, the next one first
+    writes the low 16 bits and leaves 2^8, so word q is written while coding symbol
+    2q + 1 and its record (Sec. 4.1) is the state 2^8 at index 2q."""
+    s = np.random.default_rng(N).integers(0, 256, N).astype(np.uint32)
+    words, final, ev_sym, ev_y = oracle.encode(s, np.ones(256, dtype=np.uint32), 8, 1, 16, 16)
+    assert len(words) == N // 2
+    assert np.array_equal(ev_sym, 2 * np.arange(N // 2) + 1) and np.all(ev_y == 256)
+    return ev_sym, ev_y
+
+
+@pytest.mark.parametrize("N,M,eq7,remaining", [
+    # T = ceil(100 / 3) = 34 (even): word q gives t = 2q + 1 - lo, t_s = 1, so
+    # H = |2q + 1 - lo - T| + |2q - lo - T| is 1 exactly at 2q = lo + T: q = 17, then
+    # lo = 34 and q = 34. With T over what is left the second split has
+    # T = ceil(66 / 2) = 33 (odd), where H = 1 at 2q = lo + T - 1: q = 33.
+    (100, 3, [17, 34], [17, 33]),
+    # T = 25 (odd): 2q = lo + 24 each time, q = 12, 24, 36. Left-over T: 25, then
+    # ceil(76 / 3) = 26 (2q = 24 + 26, q = 25), then ceil(50 / 2) = 25 (2q = 50 + 24, q = 37).
+    (100, 4, [12, 24, 36], [12, 25, 37]),
+    # T = ceil(99 / 3) = 33: q = 16 (m = 32), then q = 32. Left over: ceil(67 / 2) = 34, q = 33.
+    (99, 3, [16, 32], [16, 33]),
+    # T = 51: q = 25 for both (one split word only).
+    (101, 2, [25], [25]),
+])
+def test_heuristic_hand_cases(N, M, eq7, remaining):
+    """Def. 4.1 / Eq. 7 on a stream whose records are known in closed form: the split
+    words derived by hand for the printed T = ceil(N/M) and for T over the symbols left."""
+    ev_sym, ev_y = _digit_stream(N)
+    assert oracle.heuristic(ev_sym, ev_y, N, M, 1, "eq7").tolist() == eq7
+    assert oracle.heuristic(ev_sym, ev_y, N, M, 1, "remaining").tolist() == remaining
+
+
+@pytest.mark.parametrize("N", [200, 1001, 4096])
+@pytest.mark.parametrize("M", [2, 5, 16, 33])
+def test_heuristic_eq7_closed_form(N, M):
+    """On the digit stream the printed rule has a closed form: with t_s = 1, Eq. 7 is 1
+    exactly at the even owned end lo + 2 floor(T / 2), so split k ends at
+    (k + 1) 2 floor(T / 2) with T = ceil(N / M): equal splits, and the final one takes
+    what is left over."""
+    ev_sym, ev_y = _digit_stream(N)
+    T = -(-N // M)
+    want = [(k + 1) * (T // 2) for k in range(M - 1) if (k + 1) * (T // 2) < N // 2]
+    assert oracle.heuristic(ev_sym, ev_y, N, M, 1, "eq7").tolist() == want
+
+
+def test_printed_rule_piles_the_shortfall_into_the_final_split():
+    """With T = ceil(N/M) every split is short of T by about half its synchronisation
+    section and the final split collects the rest; with T over the symbols left the
+    final split stays near T (the reason the library takes that reading by default)."""
+    s = workloads.Stream("z", 1 << 18, 1, 12, "zipf", {"s": 1.2}, seed=4).symbols()
+    M = 256
+    T = -(-len(s) // M)
+    last = {}
+    for rule in ("eq7", "remaining"):
+        st = oracle.encode_with_splits(s, 12, M, rule=rule)
+        assert st.K == M
+        owned = np.diff(np.r_[0, st.idx[:-1].min(axis=1), len(s)])
+        assert owned.sum() == len(s)
+        if rule == "eq7":
+            assert owned[:-1].mean() < T                     # regular splits fall short of T on average
+        last[rule] = int(owned[-1])
+    assert last["eq7"] > 4 * T
+    assert last["remaining"] < 2 * T
 
 
 @pytest.mark.parametrize("K,Mp", [(64, 16), (64, 1), (64, 64), (65536, 148), (10, 3), (7, 20), (9, 9)])
