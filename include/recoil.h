@@ -48,11 +48,18 @@ extern "C" {
 #define RECOIL_ECUDA (-4)      /* a CUDA runtime call failed (message has the CUDA error) */
 #define RECOIL_ETIMEOUT (-5)   /* a bounded wait expired (serving runtime) */
 
+/* Split rules: the expected symbols per split T in the heuristic of Def. 4.1 / Eq. 7. */
+#define RECOIL_SPLIT_REMAINING 0u  /* T = ceil((N - lo) / (M - k)) over the symbols left (default) */
+#define RECOIL_SPLIT_EQ7 1u        /* T = ceil(N / M) for every split, as Def. 4.1 prints it */
+
 /* Coding parameters of a stream. n_bits in [1,16] (b = 16 >= n, Sec. 4.4);
- * sym_bytes 1 (uint8 symbols) or 2 (uint16 symbols). */
+ * sym_bytes 1 (uint8 symbols) or 2 (uint16 symbols); split_rule one of
+ * RECOIL_SPLIT_* (used where splits are placed; 0 = the default); reserved 0. */
 typedef struct {
   uint32_t n_bits;
   uint32_t sym_bytes;
+  uint32_t split_rule;
+  uint32_t reserved;
 } recoil_params;
 
 typedef struct recoil_stream recoil_stream;   /* opaque host object */
@@ -73,16 +80,26 @@ typedef struct {
 
 /*
  * Encode n_syms symbols as one interleaved rANS stream (Eqs. 1 and 3, Sec. 2.2)
- * and place split entries by the heuristic of Def. 4.1 / Eq. 7.
+ * and place split entries by the heuristic of Def. 4.1 / Eq. 7: for each split
+ * in turn, the usable word minimising H = |t - T| + |t - t_s - T| (t: symbols
+ * since the previous split point including this split's synchronisation
+ * section, t_s: that section's symbols; ties to the smaller word).
+ * params->split_rule picks T: RECOIL_SPLIT_EQ7 takes the printed
+ * T = ceil(N / M) for every split; RECOIL_SPLIT_REMAINING (default) takes
+ * T = ceil((N - lo) / (M - k)) over the symbols left, since with the printed T
+ * every split falls short of T by about half its synchronisation section and
+ * the shortfall collects in the final split (on 1 GiB of Zipf bytes at 65536
+ * splits: ~3.8 M symbols in the final split instead of ~16 K).
  *   syms        host array of n_syms symbols (uint8 or uint16 per params->sym_bytes)
- *   params      n_bits and sym_bytes
+ *   params      n_bits, sym_bytes and split_rule
  *   max_splits  splits M the decoder may use at most, counting the final-state
  *               entry; the heuristic yields at most M (fewer on short inputs)
  *   out         receives a new stream (free with recoil_free)
  * The static quantised PDF comes from the symbol counts (Sec. 5.1): present
  * symbols get f = max(1, round_half_even(c 2^n / N)), then +-1 corrections
  * until the sum is 2^n. Errors: RECOIL_EINVAL (null, n outside [1,16],
- * sym_bytes not 1/2, more distinct symbols than 2^n, n_syms >= 2^31),
+ * sym_bytes not 1/2, an unknown split_rule, more distinct symbols than 2^n,
+ * n_syms >= 2^31),
  * RECOIL_ENOMEM. The encoder is serial by design (Sec. 6).
  */
 int recoil_encode_with_splits(const void* syms, uint64_t n_syms, const recoil_params* params,

@@ -29,7 +29,18 @@ class RecoilError(RuntimeError):
 
 
 class Params(C.Structure):
-    _fields_ = [("n_bits", C.c_uint32), ("sym_bytes", C.c_uint32)]
+    _fields_ = [("n_bits", C.c_uint32), ("sym_bytes", C.c_uint32), ("split_rule", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+SPLIT_REMAINING, SPLIT_EQ7 = 0, 1
+_SPLIT_RULES = {"remaining": SPLIT_REMAINING, "eq7": SPLIT_EQ7}
+
+
+def _params(n_bits: int, sym_bytes: int, rule: str = "remaining") -> Params:
+    if rule not in _SPLIT_RULES:
+        raise ValueError(f"rule must be one of {tuple(_SPLIT_RULES)}")
+    return Params(n_bits, sym_bytes, _SPLIT_RULES[rule], 0)
 
 
 class Info(C.Structure):
@@ -196,30 +207,33 @@ class Stream:
         return stream_export(self)
 
 
-def recoil_encode_with_splits(symbols: np.ndarray, n_bits: int, max_splits: int) -> Stream:
+def recoil_encode_with_splits(symbols: np.ndarray, n_bits: int, max_splits: int, rule: str = "remaining") -> Stream:
+    """rule: T of Eq. 7, "remaining" (over the symbols left, default) or "eq7" (ceil(N / M) as printed)."""
     s = np.ascontiguousarray(symbols)
     if s.dtype not in (np.uint8, np.uint16):
         raise TypeError("symbols must be uint8 or uint16")
-    p = Params(n_bits, s.dtype.itemsize)
+    p = _params(n_bits, s.dtype.itemsize, rule)
     h = C.c_void_p()
     _check(lib().recoil_encode_with_splits(s.ctypes.data if s.size else None, s.size, C.byref(p),
                                            max_splits, C.byref(h)))
     return Stream(h.value)
 
 
-def recoil_encode_with_table(symbols: np.ndarray, n_bits: int, freq, max_splits: int) -> Stream:
+def recoil_encode_with_table(symbols: np.ndarray, n_bits: int, freq, max_splits: int,
+                             rule: str = "remaining") -> Stream:
     s = np.ascontiguousarray(symbols)
     if s.dtype not in (np.uint8, np.uint16):
         raise TypeError("symbols must be uint8 or uint16")
     f = np.ascontiguousarray(freq, dtype=np.uint32)
-    p = Params(n_bits, s.dtype.itemsize)
+    p = _params(n_bits, s.dtype.itemsize, rule)
     h = C.c_void_p()
     _check(lib().recoil_encode_with_table(s.ctypes.data if s.size else None, s.size, C.byref(p), _ptr(f), len(f),
                                           max_splits, C.byref(h)))
     return Stream(h.value)
 
 
-def recoil_encode_adaptive(symbols: np.ndarray, n_bits: int, tables, table_index, max_splits: int) -> Stream:
+def recoil_encode_adaptive(symbols: np.ndarray, n_bits: int, tables, table_index, max_splits: int,
+                           rule: str = "remaining") -> Stream:
     """Adaptive coding (Sec. 3.1): symbol i coded with PDF row table_index[i] of tables (T x A)."""
     s = np.ascontiguousarray(symbols)
     if s.dtype not in (np.uint8, np.uint16):
@@ -228,7 +242,7 @@ def recoil_encode_adaptive(symbols: np.ndarray, n_bits: int, tables, table_index
     t = np.ascontiguousarray(table_index, dtype=np.uint8)
     if t.shape != s.shape:
         raise ValueError("one table number per symbol")
-    p = Params(n_bits, s.dtype.itemsize)
+    p = _params(n_bits, s.dtype.itemsize, rule)
     h = C.c_void_p()
     _check(lib().recoil_encode_adaptive(s.ctypes.data if s.size else None, s.size, C.byref(p), _ptr(f), f.shape[0],
                                         f.shape[1], t.ctypes.data if t.size else None, max_splits, C.byref(h)))

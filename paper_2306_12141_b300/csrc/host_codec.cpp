@@ -153,7 +153,7 @@ void encode_loop(const T* syms, uint64_t N, const std::vector<EncSym>& tab, uint
 // forward. For a word q the backward scan of Sec. 4.1 gives, per coder, its
 // latest record at or before q; this keeps those incrementally. top is the
 // index recorded at q itself, m the smallest over coders.
-void place_splits(const Records& rec, uint64_t N, uint32_t M, std::vector<uint64_t>& out) {
+void place_splits(const Records& rec, uint64_t N, uint32_t M, uint32_t rule, std::vector<uint64_t>& out) {
   out.clear();
   const int64_t nw = (int64_t)rec.sym.size();
   if (M < 2 || nw == 0) return;
@@ -177,9 +177,10 @@ void place_splits(const Records& rec, uint64_t N, uint32_t M, std::vector<uint64
 
   int64_t lo = 0, q = 0;
   while (out.size() + 1 < M) {
-    // expected symbols per split over what is left (ceil(N / M) for the first split)
+    // expected symbols per split: over what is left (ceil(N / M) for the first
+    // split), or ceil(N / M) throughout as Def. 4.1 prints it
     const int64_t left = (int64_t)M - (int64_t)out.size();
-    const int64_t T = ((int64_t)N - lo + left - 1) / left;
+    const int64_t T = rule == RECOIL_SPLIT_EQ7 ? ((int64_t)N + M - 1) / M : ((int64_t)N - lo + left - 1) / left;
     int64_t best = -1, bestH = 0;
     for (; q < nw; q++) {
       apply(q);
@@ -297,7 +298,7 @@ static int encode_common(const void* syms, uint64_t n_syms, const recoil_params*
     }
     words->shrink_to_fit();
     std::vector<uint64_t> qs;
-    place_splits(rec, n_syms, max_splits, qs);
+    place_splits(rec, n_syms, max_splits, params->split_rule, qs);
     s->entries.resize(qs.size());
     for (size_t k = 0; k < qs.size(); k++) {
       Entry& e = s->entries[k];
@@ -322,6 +323,8 @@ static int check_params(const void* syms, uint64_t n_syms, const recoil_params* 
   if (!params || !out || (!syms && n_syms)) return fail(RECOIL_EINVAL, "null argument");
   if (params->n_bits < 1 || params->n_bits > 16) return fail(RECOIL_EINVAL, "n_bits must be in [1, 16]");
   if (params->sym_bytes != 1 && params->sym_bytes != 2) return fail(RECOIL_EINVAL, "sym_bytes must be 1 or 2");
+  if (params->split_rule != RECOIL_SPLIT_REMAINING && params->split_rule != RECOIL_SPLIT_EQ7)
+    return fail(RECOIL_EINVAL, "split_rule must be RECOIL_SPLIT_REMAINING or RECOIL_SPLIT_EQ7");
   if (n_syms >= (1ull << 31)) return fail(RECOIL_EINVAL, "streams are limited to 2^31 - 1 symbols");
   *out = nullptr;
   return RECOIL_OK;
@@ -502,6 +505,8 @@ int recoil_stream_import(const recoil_params* params, uint64_t n_syms, uint32_t 
   const uint32_t n = params->n_bits;
   if (n < 1 || n > 16) return fail(RECOIL_EINVAL, "n_bits must be in [1, 16]");
   if (params->sym_bytes != 1 && params->sym_bytes != 2) return fail(RECOIL_EINVAL, "sym_bytes must be 1 or 2");
+  if (params->split_rule != RECOIL_SPLIT_REMAINING && params->split_rule != RECOIL_SPLIT_EQ7)
+    return fail(RECOIL_EINVAL, "split_rule must be RECOIL_SPLIT_REMAINING or RECOIL_SPLIT_EQ7");
   if (alphabet < 1 || alphabet > (params->sym_bytes == 1 ? 256u : 65536u))
     return fail(RECOIL_EINVAL, "alphabet out of range");
   if (n_syms >= (1ull << 31) || n_words >= (1ull << 31)) return fail(RECOIL_EINVAL, "stream too long");

@@ -231,7 +231,7 @@ int recoil_deserialize(const void* buf, uint64_t size, recoil_stream** out) {
   const uint8_t* end = p + size;
   if (size < 12 || std::memcmp(p, "RCL1", 4) != 0) return fail(RECOIL_ECORRUPT, "not a serialised recoil stream");
   p += 4;
-  recoil_params params{p[0], p[1]};
+  recoil_params params{p[0], p[1], RECOIL_SPLIT_REMAINING, 0};
   p += 4;
   uint32_t alphabet = 0;
   if (!get_le(p, end, &alphabet) || alphabet == 0 || alphabet > 65536 ||

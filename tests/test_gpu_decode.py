@@ -53,6 +53,29 @@ def test_config1_decodes_at_64_16_1_splits(recoil_lib):
         assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(np.uint8))
 
 
+@pytest.mark.parametrize("dist,params,n,sb", [
+    ("zipf", {"s": 1.2}, 12, 1),
+    ("skewed", {"p0": 0.95}, 12, 1),
+    ("gauss16", {"mean": 2048.0, "sigma": 200.0, "k": 4096}, 15, 2),
+])
+def test_printed_rule_streams_decode_on_gpu(recoil_lib, dist, params, n, sb):
+    """Splits placed with the printed T = ceil(N/M) of Def. 4.1 (RECOIL_SPLIT_EQ7), the long
+    final split included: the library's stream and the oracle's (imported) decode to the
+    input and to the oracle's split decode at several combined counts."""
+    R = recoil_lib
+    s = workloads.Stream("t", 300_007, sb, n, dist, params, seed=37).symbols()
+    p = R.encode_with_splits(s, n, 256, rule="eq7")
+    o = oracle.encode_with_splits(s, n, 256, rule="eq7")
+    assert np.array_equal(p.export()["entry_word"].astype(np.int64), o.q)
+    imp = _import(R, o, sb)
+    for Mp in (256, 37, 4):
+        want = oracle.decode_splits(oracle.combined(o, Mp))
+        for st in (R.combine_splits(p, Mp), R.combine_splits(imp, Mp)):
+            (out,) = gpu_decode(R, [st])
+            assert np.array_equal(out, s)
+            assert np.array_equal(out, want.astype(out.dtype))
+
+
 DISTS = [
     ("laplace", {"mean": 128.0, "scale": 8.0}, 11, 1),
     ("zipf", {"s": 1.2}, 12, 1),

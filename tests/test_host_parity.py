@@ -23,9 +23,9 @@ def _cases():
     yield workloads.Stream("lap_n8", 70_001, 1, 8, "laplace", {"mean": 128.0, "scale": 3.0}, seed=26)
 
 
-def _same(R, s, n, M):
-    p = R.encode_with_splits(s, n, M)
-    o = oracle.encode_with_splits(s, n, M, alphabet=None)
+def _same(R, s, n, M, rule="remaining"):
+    p = R.encode_with_splits(s, n, M, rule=rule)
+    o = oracle.encode_with_splits(s, n, M, alphabet=None, rule=rule)
     e = p.export()
     assert np.array_equal(e["freq"], o.f)
     assert np.array_equal(e["words"], o.words)
@@ -40,6 +40,24 @@ def _same(R, s, n, M):
 @pytest.mark.parametrize("M", [1, 2, 64, 1000])
 def test_encoder_matches_oracle(recoil_lib, st, M):
     _same(recoil_lib, st.symbols(), st.n_bits, M)
+
+
+@pytest.mark.parametrize("st", list(_cases())[1:4], ids=lambda s: s.name)
+@pytest.mark.parametrize("M", [2, 64, 1000])
+def test_encoder_matches_oracle_printed_rule(recoil_lib, st, M):
+    """The printed T = ceil(N/M) of Def. 4.1 (RECOIL_SPLIT_EQ7): same split words as the oracle."""
+    _same(recoil_lib, st.symbols(), st.n_bits, M, rule="eq7")
+
+
+def test_split_rules_differ_and_default(recoil_lib):
+    """The two rules place different words on a skewed source; the default is the remaining rule."""
+    s = workloads.Stream("sk", 200_003, 1, 12, "skewed", {"p0": 0.95}, seed=22).symbols()
+    a = recoil_lib.encode_with_splits(s, 12, 64).export()["entry_word"]
+    r = recoil_lib.encode_with_splits(s, 12, 64, rule="remaining").export()["entry_word"]
+    e = recoil_lib.encode_with_splits(s, 12, 64, rule="eq7").export()["entry_word"]
+    assert np.array_equal(a, r) and not np.array_equal(r, e)
+    with pytest.raises(ValueError):
+        recoil_lib.encode_with_splits(s, 12, 64, rule="other")
 
 
 @pytest.mark.parametrize("N", [0, 1, 2, 31, 32, 33, 63, 64, 65, 100, 1023])
