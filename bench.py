@@ -65,9 +65,15 @@ def _args():
     ap.add_argument("--sweep", type=lambda v: [int(x) for x in v.split(",") if x], default=[148, 592, 2368, 9472],
                     help="zipf: split counts to sweep (empty to skip)")
     ap.add_argument("--soak", type=float, default=1.0, help="seconds of untimed steps while sampling clocks")
-    ap.add_argument("--serve-rate", type=float, default=10000.0, help="batch: serving check at this request rate")
+    ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",") if x],
+                    default=SERVE_RATES + [SATURATING_HZ],
+                    help="batch: serving request rates (Poisson, per second; the last one saturates the device)")
     ap.add_argument("--e2e-groups", type=int, default=16, help="stream groups of the end-to-end pipeline")
-    ap.add_argument("--serve-requests", type=int, default=5000, help="batch: requests in the serving check (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=20000, help="requests per serving rate (0: skip)")
+    ap.add_argument("--no-configs", action="store_true", help="batch: skip the block of the other workloads")
+    ap.add_argument("--configs-scale", type=float, default=1.0, help="shrink the other workloads (testing only)")
+    ap.add_argument("--rr-streams", type=int, default=8,
+                    help="CUDA streams of the round-robin per-stream baseline (0: skip)")
     return ap.parse_args()
 
 
@@ -304,6 +310,9 @@ SINGLE = {
 
 
 SERVE_RATES = [2000, 5000, 10000, 20000, 50000]
+# offered load far above what the device decodes: every request arrives within a few ms, so the
+# decoded GB/s is set by the device and the admission loop, not by the arrivals
+SATURATING_HZ = 10_000_000.0
 
 
 def serving(R, torch, dev, pool, rate, n_req, budget, arena, per_request):
@@ -314,15 +323,20 @@ def serving(R, torch, dev, pool, rate, n_req, budget, arena, per_request):
                       timeout_s=300.0)
     return {"p50_ms": round(st["p50_ms"], 4), "p99_ms": round(st["p99_ms"], 4), "mean_ms": round(st["mean_ms"], 4),
             "decoded_gbs": round(st["decoded_gbs"], 2), "launches": st["launches"],
-            "max_inflight": st["max_inflight"], "mean_splits": round(float(np.mean(res["splits"])), 1)}
+            "max_inflight": st["max_inflight"], "mean_splits": round(float(np.mean(res["splits"])), 1),
+            "makespan_s": round(st["makespan_s"], 4)}
 
 
 def serving_block(R, torch, dev, pool, rates, n_req, budget=20 << 30):
+    """Both arms (continuous batching, and one launch per request with every encoded split) at every
+    rate; the key of the saturating load is "saturating"."""
     arena = torch.empty(R.serve_arena_size(pool, budget), dtype=torch.uint8, device=dev)
     out = {}
     for rate in rates:
-        out[str(rate)] = {"recoil": serving(R, torch, dev, pool, rate, n_req, budget, arena, False),
-                          "per_request": serving(R, torch, dev, pool, rate, n_req, budget, arena, True)}
+        key = "saturating" if rate >= SATURATING_HZ else str(int(rate))
+        out[key] = {"recoil": serving(R, torch, dev, pool, rate, n_req, budget, arena, False),
+                    "per_request": serving(R, torch, dev, pool, rate, n_req, budget, arena, True)}
+        out[key]["offered_hz"] = rate
     del arena
     return out
 
@@ -561,6 +575,184 @@ def run_adaptive(a):
     print(json.dumps(line), flush=True)
 
 
+def time_events(fn, cs, steps: int, warmup: int) -> list[float]:
+    """Milliseconds of each of `steps` calls of fn, CUDA events on cs, after `warmup` calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        e0.record(cs)
+        fn()
+        e1.record(cs)
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def per_stream_round_robin(R, torch, dev, streams, out_ptrs, warps: int, split_symbols: int, n_cuda: int,
+                           steps: int) -> dict:
+    """Per-stream baseline with the batch's own launch shape: one launch per stream (each combined to
+    the autotuned split size, the autotuned CTA size), stream i on CUDA stream i mod n_cuda so that
+    launches of different streams overlap on the device; one step decodes every stream."""
+    main = torch.cuda.current_stream(dev)
+    groups = [list(range(g, len(streams), n_cuda)) for g in range(n_cuda)]
+    plans = [R.Plan([streams[i] for i in grp], {"warps_per_cta": warps, "split_symbols": split_symbols,
+                                                 "flags": R.BATCH_PER_STREAM}) for grp in groups]
+    wss = [torch.empty(max(256, p.workspace_size), dtype=torch.uint8, device=dev) for p in plans]
+    side = [torch.cuda.Stream(device=dev) for _ in range(n_cuda)]
+    ptrs = [[out_ptrs[i] for i in grp] for grp in groups]
+    for p, ws, c in zip(plans, wss, side):
+        p.upload(ws, stream=c)
+    torch.cuda.synchronize()
+
+    def step():
+        start = torch.cuda.Event()
+        start.record(main)
+        for p, c, pp in zip(plans, side, ptrs):
+            c.wait_event(start)
+            p.decode(pp, c)
+            done = torch.cuda.Event()
+            done.record(c)
+            main.wait_event(done)
+
+    ms = time_events(step, main, steps, 1)
+    errors = sum(p.errors(c) for p, c in zip(plans, side))
+    assert errors == 0, R.recoil_last_error()
+    return {"ms_per_step": statistics.mean(ms), "launches_per_step": sum(p.launches for p in plans),
+            "cuda_streams": n_cuda, "warps_per_cta": warps, "split_symbols": split_symbols}
+
+
+def _single_input(R, dist: str, scale: float):
+    """(symbols, encoded stream, description) of a single-stream workload (one serial encode)."""
+    make, n_full, what = SINGLE[dist]
+    st = make(int(n_full * scale))
+    s = st.symbols()
+    enc_splits = 64 if dist == "laplace" else max(1, min(65536, len(s) // 4096))
+    return s, R.encode_with_splits(s, st.n_bits, enc_splits), st.n_bits, what
+
+
+def _adaptive_input(R, scale: float):
+    st = workloads.adaptive_256mib(int((1 << 27) * scale))
+    tables = st.tables()
+    s, tid = st.draw()
+    return s, tid, R.encode_adaptive(s, st.n_bits, tables, tid, max(1, min(65536, len(s) // 4096)))
+
+
+def configs_block(R, torch, dev, cs, scale: float, steps: int, warmup: int) -> dict:
+    """Every other workload beside the batch, each decoded on the device, timed with CUDA events
+    and compared with its input on the device: the 1 MiB Laplace stream at 64 / 16 / 1 splits, the
+    1 GiB Zipf stream at 148 / 592 / 2368 / 9472 splits, the 256 MiB distribution extremes at 9472
+    splits, Recoil against conventional partitioning at 9472, and the adaptive latents at 9472.
+    `frac` is (compressed bytes in + symbol bytes out) / time against the measured HBM copy."""
+    peak = measured_peaks()["hbm_gbs"]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(6) as ex:                    # the serial encodes run side by side
+        futs = {d: ex.submit(_single_input, R, d, scale) for d in ("laplace", "zipf", "skewed", "uniform", "gauss16")}
+        fut_ad = ex.submit(_adaptive_input, R, scale)
+        single = {d: f.result() for d, f in futs.items()}
+        ad = fut_ad.result()
+    host_s = time.perf_counter() - t0
+    res = {"host_encode_s": round(host_s, 1), "scale": scale, "steps": steps, "warmup": warmup}
+
+    def run(streams, out, ref, warps, extra_in=0, tuned=False):
+        """Decode `streams` into `out` (one tensor; streams concatenated); GB/s, frac, exactness."""
+        if tuned and not warps:
+            tws = torch.empty(R.autotune_workspace_size(streams), dtype=torch.uint8, device=dev)
+            best, _ = R.autotune(streams, [out.data_ptr()], tws, tws.numel(), cs, steps=3, keep_splits=True)
+            warps = best["warps_per_cta"]
+            del tws
+        plan = R.Plan(streams, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+        ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device=dev)
+        plan.upload(ws, stream=cs)
+        offs, o = [], 0
+        for st in streams:
+            offs.append(out.data_ptr() + o)
+            o += st.info["n_syms"] * st.info["sym_bytes"]
+        out.fill_(0xAB)
+        ms = time_events(lambda: plan.decode(offs, cs), cs, steps, warmup)
+        errors = plan.errors(cs)
+        exact = bool(errors == 0 and torch.equal(out, ref))
+        nbytes = out.numel()
+        words = sum(2 * st.info["n_words"] + 4 * 32 for st in streams)
+        t = statistics.mean(ms) * 1e-3
+        r = {"gbs": round(nbytes / t / 1e9, 1), "us": round(t * 1e6, 1), "warps_per_cta": plan.warps_per_cta,
+             "splits": sum(st.info["n_entries"] for st in streams),
+             "frac": round((nbytes + words + extra_in) / t / 1e9 / peak, 4), "exact": exact}
+        del ws
+        return r
+
+    with torch.cuda.stream(cs):
+        # configuration 1: 1 MiB Laplace, encoded at 64 splits, decoded as 64, 16 and 1
+        s, enc, n, what = single["laplace"]
+        out = torch.empty(len(s), dtype=torch.uint8, device=dev)
+        ref = torch.from_numpy(s).to(dev)
+        res["laplace_1mib"] = {"workload": what, **{str(k): run([R.combine_splits(enc, k)], out, ref, 0)
+                                                   for k in (64, 16, 1)}}
+        # configuration 2: 1 GiB Zipf, 65536 encoded splits combined to the decoder's count
+        s, enc, n, what = single["zipf"]
+        out = torch.empty(len(s), dtype=torch.uint8, device=dev)
+        ref = torch.from_numpy(s).to(dev)
+        z = {"workload": what}
+        for k in (148, 592, 2368, 9472):
+            z[str(k)] = run([R.combine_splits(enc, k)], out, ref, 0)
+        z["9472_tuned"] = run([R.combine_splits(enc, 9472)], out, ref, 0, tuned=True)
+        res["zipf_1gib"] = z
+        # Recoil against the conventional scheme (Sec. 2.3): the same input cut into 9472 partitions
+        # under the same quantised model, each with its own final states; same kernel and CTA size
+        warps = z["9472_tuned"]["warps_per_cta"]
+        freq = R.stream_freq(enc)
+        parts = np.array_split(s, 9472)
+        with ThreadPoolExecutor(max(1, min(64, os.cpu_count() or 1))) as ex:
+            conv = list(ex.map(lambda q: R.encode_with_table(q, n, freq, 1), parts))
+        rec = R.combine_splits(enc, 9472)
+        res["recoil_vs_conventional"] = {
+            "workload": "1 GiB Zipf(1.2) bytes as one stream at 9472 splits vs 9472 independent partitions",
+            "recoil": run([rec], out, ref, warps), "conventional": run(conv, out, ref, warps),
+            "recoil_size_bytes": int(rec.info["bitstream_bytes"] + R.serialized_size(rec)[1]),
+            "conventional_size_bytes": int(sum(c.info["bitstream_bytes"] for c in conv) + 8 * len(conv))}
+        del conv, parts
+        # configuration 3: the distribution extremes at 9472 splits, CTA size autotuned
+        for d in ("skewed", "uniform", "gauss16"):
+            s, enc, n, what = single[d]
+            out = torch.empty(len(s) * s.itemsize, dtype=torch.uint8, device=dev)
+            ref = torch.from_numpy(s.view(np.uint8)).to(dev)
+            res[f"{d}_256mib"] = {"workload": what, "9472": run([R.combine_splits(enc, 9472)], out, ref, 0, tuned=True)}
+        # adaptive latents (Sec. 3.1) at 9472 splits: table numbers are read too
+        s, tid, enc = ad
+        out = torch.empty(len(s) * 2, dtype=torch.uint8, device=dev)
+        ref = torch.from_numpy(s.view(np.uint8)).to(dev)
+        res["adaptive_latents"] = {"workload": "2^27 uint16 latents, 64 Gaussian PDFs over 256 values, n=16",
+                                   "9472": run([R.combine_splits(enc, 9472)], out, ref, 0, extra_in=len(s), tuned=True)}
+        del out, ref
+    res["all_exact"] = all(v.get("exact", True) for blk in res.values() if isinstance(blk, dict)
+                           for v in blk.values() if isinstance(v, dict))
+    return res
+
+
+def cpu_split_parallel(R, seconds: float) -> dict:
+    """The paper's CPU recipe (Sec. 4.4, one split per core) on the oracle: the first 2^26 symbols of
+    the 1 GiB Zipf stream, encoded by the oracle at one split per host thread, decoded by the oracle's
+    split decoder with one thread per split, repeated until `seconds` of decode wall time."""
+    import oracle
+    threads = os.cpu_count() or 1
+    st = workloads.zipf_1gib(1 << 26)
+    s = st.symbols()
+    o = oracle.encode_with_splits(s, st.n_bits, threads)
+    out = np.zeros(len(s), dtype=np.uint32)
+    wall, reps = 0.0, 0
+    with ThreadPoolExecutor(threads) as ex:
+        while wall < seconds or reps < 2:
+            t = time.perf_counter()
+            list(ex.map(lambda k: oracle.decode_thread(o, k, out=out), range(o.K)))
+            wall += time.perf_counter() - t
+            reps += 1
+    assert np.array_equal(out, s)
+    return {"value": reps * len(s) / wall / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"first 2^26 symbols of the 1 GiB Zipf stream, {o.K} splits (one per thread), oracle split "
+                      f"decoder (plain C -O2), {reps} decodes"}
+
+
 def run_ours(a):
     import torch
     import paper_2306_12141_b300 as R
@@ -672,8 +864,20 @@ def run_ours(a):
             exact()
             extra["per_stream"] = {"value": out_bytes / (statistics.mean(base_ms) * 1e-3) / 1e9, "unit": "GB/s",
                                    "ms_per_step": statistics.mean(base_ms), "launches_per_step": base.launches,
-                                   "speedup": statistics.mean(base_ms) / statistics.mean(ms)}
+                                   "speedup": statistics.mean(base_ms) / statistics.mean(ms),
+                                   "shape": "one launch per stream on one CUDA stream, 4-warp CTAs, every "
+                                            "encoded split (the paper's launch)"}
             del bws
+            if a.rr_streams > 0:
+                rr = per_stream_round_robin(R, torch, dev, streams, out_ptrs, warps, split_symbols or 65536,
+                                            a.rr_streams, a.per_stream_steps)
+                exact()
+                rr["value"] = out_bytes / (rr["ms_per_step"] * 1e-3) / 1e9
+                rr["unit"] = "GB/s"
+                rr["speedup"] = rr["ms_per_step"] / statistics.mean(ms)
+                rr["shape"] = (f"one launch per stream at the batch's split size and CTA size, stream i on "
+                               f"CUDA stream i mod {a.rr_streams}")
+                extra["per_stream"]["round_robin"] = rr
 
         if not batch and a.sweep:
             sweep = {}
@@ -689,10 +893,14 @@ def run_ours(a):
             exact()
             extra["split_sweep_gbs"] = sweep
 
-        if batch and a.serve_requests > 0:
-            # continuous-batching serving over the same pool (Poisson arrivals, 20 GiB budget)
-            extra["serving"] = {"requests": a.serve_requests, "budget_gib": 20,
-                                "rates_hz": serving_block(R, torch, dev, streams, [a.serve_rate], a.serve_requests)}
+        if batch and a.serve_requests > 0 and a.serve_rates:
+            # continuous-batching serving over the same pool (Poisson arrivals, 20 GiB budget), both
+            # arms at every rate, the last rate saturating the device
+            extra["serving"] = {"requests_per_rate": a.serve_requests, "budget_gib": 20,
+                                "rates_hz": serving_block(R, torch, dev, streams, a.serve_rates, a.serve_requests)}
+
+        if batch and not a.no_configs and world == 1:
+            extra["configs"] = configs_block(R, torch, dev, cs, a.configs_scale, 10, 3)
 
         e2e = None
         if not a.no_e2e:
@@ -759,6 +967,7 @@ def run_ours(a):
     if rank == 0 and not a.no_cpu:
         if batch:
             line["cpu_baseline"] = cpu_baseline(specs, syms, a.cpu_seconds)
+            line["cpu_baseline"]["split_parallel"] = cpu_split_parallel(R, max(2.0, a.cpu_seconds / 2))
         else:                                             # the oracle sees the stream in 16 Mi-symbol pieces
             piece = 1 << 24
             parts = [syms[0][i:i + piece] for i in range(0, min(len(syms[0]), 64 * piece), piece)]
@@ -778,10 +987,10 @@ def run_serve(a):
     specs, syms, streams = build_batch(R, a.streams, a.scale)
     n_req = a.serve_requests if a.serve_requests > 0 else 20000
     with Clocks(dev.index) as clk:
-        sweep = serving_block(R, torch, dev, streams, SERVE_RATES, n_req)
+        sweep = serving_block(R, torch, dev, streams, a.serve_rates, n_req)
     top = sweep[str(SERVE_RATES[-1])]
     line = {"metric": METRIC, "value": top["recoil"]["decoded_gbs"], "unit": "GB/s", "n_gpus": 1,
-            "steps": len(SERVE_RATES), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "steps": len(a.serve_rates), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals over the " + BATCH_WORKLOAD + ", 20 GiB budget",
                        "requests_per_rate": n_req},
@@ -805,8 +1014,6 @@ if __name__ == "__main__":
     elif args.workload == "adaptive":
         run_adaptive(args)
     elif args.workload == "serve":
-        if args.serve_requests == 5000:
-            args.serve_requests = 20000
         run_serve(args)
     else:
         run_ours(args)

@@ -35,6 +35,8 @@
 // a fault or a hang.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "device_types.h"
@@ -457,20 +459,43 @@ size_t smem_bytes(uint32_t warps, uint32_t table_smem) {
   return (size_t)table_smem + (size_t)warps * kRingSlots * sizeof(uint16_t);
 }
 
+// The dynamic shared memory a kernel may use is raised only when a launch
+// needs more than was allowed before on that device: setting the attribute is
+// a host call of several microseconds, too slow to repeat for every launch
+// when one stream is decoded per launch. The value kept per device is only a
+// hint: a launch that fails raises the attribute again and retries once (a
+// device reset drops the attribute, not this record).
+constexpr int kMaxDevices = 64;
+
+template <uint32_t KIND, int WARPS>
+cudaError_t allow_smem(size_t sm, bool force) {
+  static std::atomic<int> allowed[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = -1;
+  if (!force && dev >= 0 && allowed[dev].load(std::memory_order_relaxed) >= (int)sm) return cudaSuccess;
+  const int want = dev >= 0 && !force ? std::max<int>((int)sm, allowed[dev].load(std::memory_order_relaxed)) : (int)sm;
+  const cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  if (e == cudaSuccess && dev >= 0) allowed[dev].store(want, std::memory_order_relaxed);
+  return e;
+}
+
 template <uint32_t KIND, int WARPS>
 cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   const size_t sm = smem_bytes(WARPS, a.table_smem);
-  cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  decode_kernel<KIND, WARPS><<<grid, WARPS * 32, sm, s>>>(a);
-  return cudaGetLastError();
+  for (int attempt = 0; attempt < 2; attempt++) {
+    cudaError_t e = allow_smem<KIND, WARPS>(sm, attempt > 0);
+    if (e != cudaSuccess) return e;
+    decode_kernel<KIND, WARPS><<<grid, WARPS * 32, sm, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaErrorInvalidValue || attempt > 0) return e;
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <uint32_t KIND, int WARPS>
 int occupancy_kw(uint32_t table_smem, int* out) {
   const size_t sm = smem_bytes(WARPS, table_smem);
-  if (cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-    return -1;
+  if (allow_smem<KIND, WARPS>(sm, false) != cudaSuccess) return -1;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
 }
 
