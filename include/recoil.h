@@ -235,6 +235,9 @@ typedef struct {
 #define RECOIL_BATCH_GRAPH 4u        /* capture the launch sequence in a CUDA graph on the first
                                         recoil_plan_decode and replay it afterwards (needs a
                                         non-default cuda_stream; ignored with PER_STREAM) */
+#define RECOIL_BATCH_NO_PAIRS 8u     /* adaptive models over up to 256 symbols: stage the one-byte
+                                        guide layout even where the paired one (one read for the
+                                        bracket, one for F and f) fits as well */
 
 typedef struct recoil_plan recoil_plan;   /* opaque: device image layout + work queue of a batch */
 
@@ -276,6 +279,17 @@ uint32_t recoil_plan_launches(const recoil_plan* plan);
 
 /* Warps per CTA the plan decodes with (the automatic choice when opts gave 0). */
 uint32_t recoil_plan_warps_per_cta(const recoil_plan* plan);
+
+/* Decoder kernels a plan launches, one bit each (host only, no device call). */
+#define RECOIL_KERNEL_PACKED8 1u          /* 8-bit symbols, n <= 12: one packed u32 per slot */
+#define RECOIL_KERNEL_GENERIC8 2u         /* 8-bit symbols otherwise: slot -> symbol, symbol -> (f, F) */
+#define RECOIL_KERNEL_GENERIC16 4u        /* 16-bit symbols, static model */
+#define RECOIL_KERNEL_ADAPTIVE8 8u        /* adaptive, 8-bit symbols, one-byte guide entries */
+#define RECOIL_KERNEL_ADAPTIVE16 16u      /* adaptive, 16-bit symbols, alphabet <= 256, one-byte guide entries */
+#define RECOIL_KERNEL_ADAPTIVE16_WIDE 32u /* adaptive, alphabet <= 4096, two-byte guide entries */
+#define RECOIL_KERNEL_ADAPTIVE8_PAIR 64u  /* adaptive, 8-bit symbols, paired layout */
+#define RECOIL_KERNEL_ADAPTIVE16_PAIR 128u /* adaptive, 16-bit symbols, alphabet <= 256, paired layout */
+uint32_t recoil_plan_kernels(const recoil_plan* plan);
 
 void recoil_plan_free(recoil_plan* plan);
 

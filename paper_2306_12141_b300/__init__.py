@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(HERE, "librecoil.so")
 
 W = 32
 OK, EINVAL, ECORRUPT, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
-BATCH_PER_STREAM, BATCH_NO_SORT, BATCH_GRAPH = 1, 2, 4
+BATCH_PER_STREAM, BATCH_NO_SORT, BATCH_GRAPH, BATCH_NO_PAIRS = 1, 2, 4, 8
+(KERNEL_PACKED8, KERNEL_GENERIC8, KERNEL_GENERIC16, KERNEL_ADAPTIVE8, KERNEL_ADAPTIVE16, KERNEL_ADAPTIVE16_WIDE,
+ KERNEL_ADAPTIVE8_PAIR, KERNEL_ADAPTIVE16_PAIR) = (1 << k for k in range(8))
 
 
 class RecoilError(RuntimeError):
@@ -92,7 +94,7 @@ EXPORTS = [
     "recoil_pipeline_create", "recoil_pipeline_sizes", "recoil_pipeline_run", "recoil_pipeline_errors",
     "recoil_pipeline_free", "recoil_shard", "recoil_encode_with_table",
     "recoil_serialized_size", "recoil_serialize", "recoil_deserialize", "recoil_encode_adaptive",
-    "recoil_plan_create_shard", "recoil_plan_warps_per_cta",
+    "recoil_plan_create_shard", "recoil_plan_warps_per_cta", "recoil_plan_kernels",
 ]
 
 _lib = None
@@ -130,6 +132,8 @@ def lib():
         L.recoil_plan_warps_per_cta.argtypes = [vp]
         L.recoil_plan_warps_per_cta.restype = u32
         L.recoil_plan_launches.restype = u32
+        L.recoil_plan_kernels.argtypes = [vp]
+        L.recoil_plan_kernels.restype = u32
         L.recoil_plan_free.argtypes = [vp]
         L.recoil_plan_free.restype = None
         L.recoil_workspace_size.argtypes = [vp, u32, C.POINTER(BatchOpts), C.POINTER(C.c_size_t)]
@@ -400,6 +404,11 @@ class Plan:
         return int(lib().recoil_plan_launches(self.handle))
 
     @property
+    def kernels(self) -> int:
+        """Bit mask of the decoder kernels the plan launches (KERNEL_*)."""
+        return int(lib().recoil_plan_kernels(self.handle))
+
+    @property
     def warps_per_cta(self) -> int:
         return int(lib().recoil_plan_warps_per_cta(self.handle))
 
@@ -471,6 +480,10 @@ def recoil_plan_errors(plan: Plan, cuda_stream=None) -> int:
 
 def recoil_plan_launches(plan: Plan) -> int:
     return plan.launches
+
+
+def recoil_plan_kernels(plan: Plan) -> int:
+    return plan.kernels
 
 
 def recoil_plan_free(plan: Plan) -> None:

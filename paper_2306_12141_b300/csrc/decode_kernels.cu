@@ -129,6 +129,41 @@ struct AdaptiveTables {
   }
 };
 
+// Adaptive model, paired layout (alphabets up to 256): row t holds for every
+// symbol s the u32 H(s) | H(s+1) << 16, with H as above, and guide entry b of
+// row t the u16 lo | hi << 8 of the symbols owning the first slots of buckets
+// b and b + 1 (2^9 buckets): one read brackets the symbol, one read of the
+// row gives F(s) and f(s) once the bracket is closed.
+struct PairTables {
+  const uint32_t* pairs;
+  const uint16_t* guide;
+  uint32_t stride, gstride, gshift;
+  __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream& st) {
+    pairs = reinterpret_cast<const uint32_t*>(smem);
+    guide = reinterpret_cast<const uint16_t*>(smem + (size_t)st.n_tables * st.row_stride * 4);
+    stride = st.row_stride;
+    gstride = st.guide_stride / 2;
+    gshift = st.n_bits > st.guide_bits ? st.n_bits - st.guide_bits : 0;
+  }
+  __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask, uint32_t t) const {
+    const uint32_t slot = x & mask;
+    const uint32_t* row = pairs + t * stride;
+    const uint32_t g = guide[t * gstride + (slot >> gshift)];
+    uint32_t s = g & 0xffu;
+    uint32_t hi = g >> 8;
+    const uint16_t* low = reinterpret_cast<const uint16_t*>(row);   // H(s) at low[2 s] (little-endian)
+    while (s < hi) {                                    // bounded: hi - s halves
+      const uint32_t mid = (s + hi + 1) >> 1;
+      if (low[2 * mid] < slot) s = mid; else hi = mid - 1;
+    }
+    const uint32_t p = row[s];
+    const uint32_t h0 = p & 0xffffu;
+    const uint32_t f = ((p >> 16) - h0) & 0xffffu;
+    x = f * (x >> n) + slot - ((h0 + 1u) & 0xffffu);
+    return s;
+  }
+};
+
 template <uint32_t KIND>
 __host__ __device__ constexpr bool is_adaptive() {
   return is_adaptive_kind(KIND);
@@ -141,7 +176,9 @@ struct TablesOf {
 };
 template <uint32_t KIND>
 struct TablesOf<KIND, true> {
-  using T = AdaptiveTables<typename std::conditional<adaptive_guide_entry_bytes(KIND) == 2, uint16_t, uint8_t>::type>;
+  using T = typename std::conditional<
+      is_pair_kind(KIND), PairTables,
+      AdaptiveTables<typename std::conditional<adaptive_guide_entry_bytes(KIND) == 2, uint16_t, uint8_t>::type>>::type;
 };
 
 template <uint32_t KIND>
@@ -158,6 +195,10 @@ struct SymOut<kAdaptive16> {
 };
 template <>
 struct SymOut<kAdaptive16Wide> {
+  using T = uint16_t;
+};
+template <>
+struct SymOut<kAdaptive16Pair> {
   using T = uint16_t;
 };
 
@@ -558,6 +599,8 @@ cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cud
     case kAdaptive8: return launch_k<kAdaptive8>(a, grid, s);
     case kAdaptive16: return launch_k<kAdaptive16>(a, grid, s);
     case kAdaptive16Wide: return launch_k<kAdaptive16Wide>(a, grid, s);
+    case kAdaptive8Pair: return launch_k<kAdaptive8Pair>(a, grid, s);
+    case kAdaptive16Pair: return launch_k<kAdaptive16Pair>(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -570,6 +613,8 @@ int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, in
     case kAdaptive8: return occupancy_k<kAdaptive8>(warps, table_smem, out);
     case kAdaptive16: return occupancy_k<kAdaptive16>(warps, table_smem, out);
     case kAdaptive16Wide: return occupancy_k<kAdaptive16Wide>(warps, table_smem, out);
+    case kAdaptive8Pair: return occupancy_k<kAdaptive8Pair>(warps, table_smem, out);
+    case kAdaptive16Pair: return occupancy_k<kAdaptive16Pair>(warps, table_smem, out);
   }
   return -1;
 }

@@ -31,18 +31,39 @@ enum TableKind : uint32_t {
   kAdaptive8 = 3,       // 8-bit symbols; one-byte guide entries
   kAdaptive16 = 4,      // 16-bit symbols, alphabet <= 256; one-byte guide entries
   kAdaptive16Wide = 5,  // 16-bit symbols, alphabet <= 4096; two-byte guide entries
-  kKinds = 6,
+  // the same models as kAdaptive8 / kAdaptive16 in the paired layout: one u32
+  // per symbol holding H(s) and H(s+1), one u16 per guide bucket holding both
+  // bracketing symbols, so a symbol costs two shared reads when the bucket
+  // decides it (a plan stages it where it keeps as many splits resident)
+  kAdaptive8Pair = 6,
+  kAdaptive16Pair = 7,
+  kKinds = 8,
 };
 
+static_assert(RECOIL_KERNEL_PACKED8 == 1u << kPacked8 && RECOIL_KERNEL_GENERIC8 == 1u << kGeneric8 &&
+                  RECOIL_KERNEL_GENERIC16 == 1u << kGeneric16 && RECOIL_KERNEL_ADAPTIVE8 == 1u << kAdaptive8 &&
+                  RECOIL_KERNEL_ADAPTIVE16 == 1u << kAdaptive16 &&
+                  RECOIL_KERNEL_ADAPTIVE16_WIDE == 1u << kAdaptive16Wide &&
+                  RECOIL_KERNEL_ADAPTIVE8_PAIR == 1u << kAdaptive8Pair &&
+                  RECOIL_KERNEL_ADAPTIVE16_PAIR == 1u << kAdaptive16Pair,
+              "kernel bits follow the table kinds");
+
 __host__ __device__ constexpr bool is_adaptive_kind(uint32_t k) { return k >= kAdaptive8 && k < kKinds; }
+__host__ __device__ constexpr bool is_pair_kind(uint32_t k) { return k == kAdaptive8Pair || k == kAdaptive16Pair; }
+// The paired kind of an adaptive kind with one-byte guide entries (itself otherwise).
+__host__ __device__ constexpr uint32_t pair_kind_of(uint32_t k) {
+  return k == kAdaptive8 ? kAdaptive8Pair : k == kAdaptive16 ? kAdaptive16Pair : k;
+}
 // Bytes of a guide entry (a symbol number) of an adaptive kind.
 __host__ __device__ constexpr uint32_t adaptive_guide_entry_bytes(uint32_t k) { return k == kAdaptive16Wide ? 2 : 1; }
 // The guide of a row: 2^g buckets over the 2^n slots (at most 2^n). A plan
 // stages g = 9, or 10 where it can afford twice the guide's shared memory,
-// or 0 (one bucket: the whole row is searched) where even 9 does not fit.
+// or 0 (one bucket: the whole row is searched) where even 9 does not fit, or
+// the paired layout with 2^9 buckets (kGuidePairs, for one-byte entries).
 constexpr uint32_t kGuideBits = 9;
 constexpr uint32_t kGuideBitsFine = 10;
 constexpr uint32_t kGuideBitsNone = 0;
+constexpr uint32_t kGuidePairs = 0x100 | kGuideBits;   // variant code, not a width: 2^9 buckets, paired
 
 // Longest alphabet of an adaptive model (the decoder's CDF search covers 2^12 symbols).
 constexpr uint32_t kMaxAdaptiveAlphabet = 4096;
@@ -79,7 +100,8 @@ struct alignas(16) DevStream {
     uint32_t slot_bytes;     // generic kinds: bytes of the slot -> symbol part (multiple of 16)
     uint32_t guide_bits;     // adaptive kinds: log2 of the guide buckets per row
   };
-  uint32_t row_stride;       // adaptive: 16-bit entries between CDF rows (odd number of 32-bit words)
+  uint32_t row_stride;       // adaptive: entries between CDF rows, an odd number of 32-bit words
+                             // (16-bit entries; paired kinds: 32-bit entries)
   uint32_t n_tables;         // adaptive: CDF rows
   uint32_t guide_stride;     // adaptive kinds: bytes between guide rows (after all CDF rows; one entry per bucket boundary)
 };

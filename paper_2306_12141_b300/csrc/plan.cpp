@@ -50,18 +50,38 @@ uint32_t guide_stride(uint32_t n, uint32_t g, uint32_t eb) {
   return 4 * words;
 }
 
-// An adaptive stream's table image holds three variants, each the CDF rows
-// followed by a guide row per PDF: 2^9 buckets, 2^10 buckets, one bucket; a
-// plan stages one of them. The guide widths in image order:
-constexpr uint32_t kGuideVariants[3] = {kGuideBits, kGuideBitsFine, kGuideBitsNone};
+// Paired layout (one-byte guide entries only): u32 entries between CDF rows
+// (one per symbol, H(s) | H(s+1) << 16), an odd number so that rows start in
+// different banks, and bytes between guide rows (2^g u16 entries, g = 9 or n).
+uint32_t pair_row_stride(uint32_t A) { return A | 1u; }
+uint32_t pair_guide_stride(uint32_t n) {
+  uint32_t words = ((1u << guide_bits(n, kGuideBits)) * 2 + 3) / 4;
+  if (!(words & 1)) words++;
+  return 4 * words;
+}
 
-// Offset and size of the variant with guide width g within the image.
-void guide_variant(const Stream& s, uint32_t g, size_t* off, size_t* bytes) {
-  const size_t rows = (size_t)s.n_tables * adaptive_row_stride(s.alphabet()) * 2;
+// An adaptive stream's table image holds four variants: the CDF rows followed
+// by a guide row per PDF with 2^9 buckets, with 2^10 buckets, with one bucket,
+// and (one-byte guide entries only) the paired layout with 2^9 buckets; a
+// plan stages one of them. The variants in image order:
+constexpr uint32_t kGuideVariants[4] = {kGuideBits, kGuideBitsFine, kGuideBitsNone, kGuidePairs};
+
+// Bytes of the variant `v` of a stream's image (0: not built for this model).
+size_t variant_bytes(const Stream& s, uint32_t v) {
   const uint32_t eb = adaptive_guide_entry_bytes(table_kind_of(s));
+  if (v == kGuidePairs) {
+    if (eb != 1) return 0;
+    return align_up((size_t)s.n_tables * ((size_t)pair_row_stride(s.alphabet()) * 4 + pair_guide_stride(s.n_bits)), 16);
+  }
+  const size_t rows = (size_t)s.n_tables * adaptive_row_stride(s.alphabet()) * 2;
+  return align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, v, eb), 16);
+}
+
+// Offset and size of the variant `g` within the image.
+void guide_variant(const Stream& s, uint32_t g, size_t* off, size_t* bytes) {
   size_t o = 0;
   for (uint32_t v : kGuideVariants) {
-    const size_t b = align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, v, eb), 16);
+    const size_t b = variant_bytes(s, v);
     if (v == g) {
       *off = o;
       *bytes = b;
@@ -97,6 +117,7 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
       s.table_img.assign(total, 0);
       std::vector<uint32_t> F(A + 1);
       for (uint32_t v : kGuideVariants) {
+        if (v == kGuidePairs) continue;
         guide_variant(s, v, &off, &bytes);
         uint16_t* cdf = reinterpret_cast<uint16_t*>(s.table_img.data() + off);
         uint8_t* guide = s.table_img.data() + off + rows_bytes;
@@ -113,6 +134,30 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
             e[0] = (uint8_t)sym;
             if (eb == 2) e[1] = (uint8_t)(sym >> 8);       // little-endian 16-bit entry
           }
+        }
+      }
+      if (eb == 1) {
+        // paired layout: u32 H(s) | H(s+1) << 16 per symbol, then per bucket the
+        // u16 owner(first slot of b) | owner(first slot of b + 1) << 8
+        guide_variant(s, kGuidePairs, &off, &bytes);
+        const uint32_t pstride = pair_row_stride(A), gb = guide_bits(n, kGuideBits);
+        uint32_t* prow = reinterpret_cast<uint32_t*>(s.table_img.data() + off);
+        uint16_t* pguide = reinterpret_cast<uint16_t*>(s.table_img.data() + off + (size_t)s.n_tables * pstride * 4);
+        const uint32_t gstride = pair_guide_stride(n) / 2;
+        std::vector<uint32_t> owner((1u << gb) + 1);
+        for (uint32_t t = 0; t < s.n_tables; t++) {
+          F[0] = 0;
+          for (uint32_t sym = 0; sym < A; sym++) F[sym + 1] = F[sym] + s.freq[(size_t)t * A + sym];
+          for (uint32_t sym = 0; sym < A; sym++)
+            prow[(size_t)t * pstride + sym] = ((F[sym] - 1) & 0xffffu) | (((F[sym + 1] - 1) & 0xffffu) << 16);
+          uint32_t sym = 0;
+          for (uint32_t b = 0; b <= (1u << gb); b++) {
+            const uint32_t slot = std::min<uint32_t>(b << (n - gb), (1u << n) - 1);
+            while (F[sym + 1] <= slot) sym++;
+            owner[b] = sym;
+          }
+          for (uint32_t b = 0; b < (1u << gb); b++)
+            pguide[(size_t)t * gstride + b] = (uint16_t)(owner[b] | (owner[b + 1] << 8));
         }
       }
     } else if (k == kPacked8) {
@@ -261,8 +306,12 @@ static uint64_t adaptive_ctas_per_sm(uint32_t warps, size_t smem) {
 // one bucket where not even the 2^9 guide fits beside the decoder rings.
 static void choose_guides(const recoil_plan* P, uint32_t* guide) {
   uint64_t entries[kKinds] = {};
-  size_t coarse[kKinds] = {}, fine[kKinds] = {};
-  for (uint32_t k = 0; k < kKinds; k++) guide[k] = kGuideBits;
+  size_t coarse[kKinds] = {}, fine[kKinds] = {}, paired[kKinds] = {};
+  bool pairable[kKinds];
+  for (uint32_t k = 0; k < kKinds; k++) {
+    guide[k] = kGuideBits;
+    pairable[k] = true;
+  }
   for (const Stream* s : P->streams) {
     const uint32_t k = table_kind_of(*s);
     if (!is_adaptive_kind(k)) continue;
@@ -272,6 +321,9 @@ static void choose_guides(const recoil_plan* P, uint32_t* guide) {
     coarse[k] = std::max(coarse[k], bytes);
     guide_variant(*s, kGuideBitsFine, &off, &bytes);
     fine[k] = std::max(fine[k], bytes);
+    guide_variant(*s, kGuidePairs, &off, &bytes);
+    paired[k] = std::max(paired[k], bytes);
+    pairable[k] = pairable[k] && bytes > 0;
   }
   const size_t rings = (size_t)P->warps * ring_smem_per_warp() + 16;
   const uint64_t sms = (uint64_t)device_sms();
@@ -281,10 +333,20 @@ static void choose_guides(const recoil_plan* P, uint32_t* guide) {
       guide[k] = kGuideBitsNone;
       continue;
     }
-    if (fine[k] + rings > kMaxSmem) continue;
-    const uint64_t cap9 = adaptive_ctas_per_sm(P->warps, coarse[k] + rings) * sms * P->warps;
-    const uint64_t cap10 = adaptive_ctas_per_sm(P->warps, fine[k] + rings) * sms * P->warps;
-    if (std::min(entries[k], cap10) >= std::min(entries[k], cap9)) guide[k] = kGuideBitsFine;
+    // the variant that keeps the most splits resident; on a tie the finer
+    // guide, and the paired layout before either
+    uint64_t best = std::min(entries[k], adaptive_ctas_per_sm(P->warps, coarse[k] + rings) * sms * P->warps);
+    if (fine[k] + rings <= kMaxSmem) {
+      const uint64_t cap10 = std::min(entries[k], adaptive_ctas_per_sm(P->warps, fine[k] + rings) * sms * P->warps);
+      if (cap10 >= best) {
+        guide[k] = kGuideBitsFine;
+        best = cap10;
+      }
+    }
+    if (pairable[k] && !(P->opts.flags & RECOIL_BATCH_NO_PAIRS) && paired[k] + rings <= kMaxSmem) {
+      const uint64_t capp = std::min(entries[k], adaptive_ctas_per_sm(P->warps, paired[k] + rings) * sms * P->warps);
+      if (capp >= best) guide[k] = kGuidePairs;
+    }
   }
 }
 
@@ -315,6 +377,8 @@ static int plan_build(recoil_plan* P) {
     const Stream& s = *P->streams[i];
     uint32_t kind = 0, slot_bytes = 0;
     const std::vector<uint8_t>& img = table_image(s, &kind, &slot_bytes);
+    const uint32_t base_kind = kind;                  // the model's kind; the staged layout may pair it
+    if (is_adaptive_kind(kind) && guide[kind] == kGuidePairs) kind = pair_kind_of(kind);
     DevStream& d = ds[i];
     std::memset(&d, 0, sizeof d);
     d.words = word_off;
@@ -370,16 +434,23 @@ static int plan_build(recoil_plan* P) {
         }
       }
       d.tid = (int64_t)word_off - (int64_t)(tlo / 2);
-      d.row_stride = adaptive_row_stride(s.alphabet());
       d.n_tables = s.n_tables;
       {
-        // stage the variant of the plan's guide width
+        // stage the variant of the plan's guide width (or the paired layout)
+        const uint32_t g = guide[base_kind];
         size_t voff = 0, vbytes = 0;
-        guide_variant(s, guide[kind], &voff, &vbytes);
+        guide_variant(s, g, &voff, &vbytes);
         d.table += voff;
         d.table_bytes = (uint32_t)vbytes;
-        d.guide_bits = guide_bits(s.n_bits, guide[kind]);
-        d.guide_stride = guide_stride(s.n_bits, guide[kind], adaptive_guide_entry_bytes(kind));
+        if (g == kGuidePairs) {
+          d.row_stride = pair_row_stride(s.alphabet());
+          d.guide_bits = guide_bits(s.n_bits, kGuideBits);
+          d.guide_stride = pair_guide_stride(s.n_bits);
+        } else {
+          d.row_stride = adaptive_row_stride(s.alphabet());
+          d.guide_bits = guide_bits(s.n_bits, g);
+          d.guide_stride = guide_stride(s.n_bits, g, adaptive_guide_entry_bytes(base_kind));
+        }
       }
       P->tid_off[i] = word_off;
       P->tid_lo[i] = tlo;
@@ -784,6 +855,14 @@ int recoil_plan_errors(recoil_plan* P, void* stream, uint32_t* flags) {
 uint32_t recoil_plan_launches(const recoil_plan* P) { return P ? P->launches : 0; }
 
 uint32_t recoil_plan_warps_per_cta(const recoil_plan* P) { return P ? P->warps : 0; }
+
+uint32_t recoil_plan_kernels(const recoil_plan* P) {
+  if (!P) return 0;
+  uint32_t m = 0;
+  for (uint32_t k = 0; k < kKinds; k++)
+    if (P->kind_count[k]) m |= 1u << k;
+  return m;
+}
 
 void recoil_plan_free(recoil_plan* P) { delete P; }
 

@@ -150,6 +150,54 @@ def test_gpu_adaptive_matches_oracle(recoil_lib, cfg):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("cfg", [c for c in CASES if c["alphabet"] <= 256],
+                         ids=lambda c: f"n{c['n_bits']}_A{c['alphabet']}_T{c['n_tables']}")
+@pytest.mark.parametrize("warps", [8, 32])
+def test_gpu_adaptive_paired_and_byte_layouts(recoil_lib, cfg, warps):
+    """Alphabets up to 256 have two staged layouts: the paired one (u32 H(s) | H(s+1) << 16
+    per symbol, a u16 bracket per guide bucket) where it keeps as many splits resident, and
+    the one-byte guide layout (RECOIL_BATCH_NO_PAIRS forces it). Both decode to the input
+    and to the oracle's split decode; the paired image is the larger one when it is staged."""
+    R = recoil_lib
+    a, tables, s, tid = _case(300_007, 26, **cfg)
+    p = R.encode_adaptive(s, cfg["n_bits"], tables, tid, 512)
+    o = oracle.encode_adaptive_with_splits(s, tid, tables, cfg["n_bits"], 512)
+    pair = R.KERNEL_ADAPTIVE8_PAIR if cfg["sym_bytes"] == 1 else R.KERNEL_ADAPTIVE16_PAIR
+    byte = R.KERNEL_ADAPTIVE8 if cfg["sym_bytes"] == 1 else R.KERNEL_ADAPTIVE16
+    seen = set()
+    for flags in (0, R.BATCH_NO_PAIRS, R.BATCH_NO_PAIRS | R.BATCH_GRAPH, R.BATCH_GRAPH):
+        for Mp in (512, 41):
+            c = R.combine_splits(p, Mp)
+            kernels = R.Plan([c], {"warps_per_cta": warps, "flags": flags}).kernels
+            assert kernels in (pair, byte)
+            assert kernels == byte or not flags & R.BATCH_NO_PAIRS
+            seen.add(kernels)
+            (out,) = _gpu_decode(R, [c], {"warps_per_cta": warps, "flags": flags})
+            assert np.array_equal(out, s), (flags, Mp)
+            assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(out.dtype)), (flags, Mp)
+    assert seen == {pair, byte}
+
+
+def test_adaptive_paired_layout_staged_where_it_fits(recoil_lib):
+    """Host side of the layout choice: 64 PDFs over 256 symbols at n = 16 take 132 KB paired,
+    which fits beside the rings of one 32-warp CTA (as the 2^10-bucket byte layout does), so
+    the paired image is staged; RECOIL_BATCH_NO_PAIRS stages the byte layout instead."""
+    R = recoil_lib
+    a, tables, s, tid = _case(20_000, 27)
+    p = R.encode_adaptive(s, 16, tables, tid, 64)
+    assert R.Plan([p], {"warps_per_cta": 32}).kernels == R.KERNEL_ADAPTIVE16_PAIR
+    assert R.Plan([p], {"warps_per_cta": 32, "flags": R.BATCH_NO_PAIRS}).kernels == R.KERNEL_ADAPTIVE16
+    # 256 PDFs: 264 KB paired, more than the shared memory; the byte layout (one-bucket guide) stays
+    a, tables, s, tid = _case(20_000, 28, n_tables=256)
+    p = R.encode_adaptive(s, 16, tables, tid, 64)
+    assert R.Plan([p], {"warps_per_cta": 8}).kernels == R.KERNEL_ADAPTIVE16
+    # wide alphabets have no paired layout
+    a, tables, s, tid = _case(20_000, 29, n_tables=4, alphabet=1000)
+    p = R.encode_adaptive(s, 16, tables, tid, 64)
+    assert R.Plan([p], {"warps_per_cta": 32}).kernels == R.KERNEL_ADAPTIVE16_WIDE
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("warps", [4, 8, 16, 32])
 def test_gpu_adaptive_cta_sizes_and_graph(recoil_lib, warps):
     R = recoil_lib
