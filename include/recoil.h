@@ -238,6 +238,12 @@ typedef struct {
 #define RECOIL_BATCH_NO_PAIRS 8u     /* adaptive models over up to 256 symbols: stage the one-byte
                                         guide layout even where the paired one (one read for the
                                         bracket, one for F and f) fits as well */
+#define RECOIL_BATCH_TWO_LANES 16u   /* two coder lanes a thread: each warp decodes two splits at
+                                        once, thread j carrying coder j of both (two independent
+                                        chains of dependent reads per thread, a word ring per
+                                        split); warps_per_cta 4, 8 or 16 for static models, 8, 16
+                                        or 24 for adaptive ones; split counts round to whole
+                                        CTAs of 2 * warps_per_cta splits */
 
 typedef struct recoil_plan recoil_plan;   /* opaque: device image layout + work queue of a batch */
 

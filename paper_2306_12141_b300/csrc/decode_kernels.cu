@@ -314,6 +314,137 @@ struct EntryDecoder {
     renorm(w, w.x < kL);
   }
 
+  // Where one split's walk stands between its phases.
+  struct Span {
+    int g;             // next group to visit (decreasing)
+    int steady_lo;     // lowest group of the steady loop
+    bool bad;          // a state differed from the previous entry's record
+  };
+
+  // Prologue and synchronisation phase of entry `ent`: stages its first word
+  // chunks and walks the groups before every coder has joined, leaving g at
+  // the first group of the steady loop. False for an empty owned range.
+  __device__ __forceinline__ bool begin(const DevEntry* __restrict__ ent, Walker& w, Span& sp) {
+    const int lo = (int)ent->lo, hi1 = (int)ent->hi1;
+    if (lo >= hi1) return false;
+    const int act = ent->act[lane];
+    const uint32_t x0 = ent->x0[lane];
+    int g = ent->g_top;
+
+    w.x = 0;
+    w.p = ent->q;
+    w.cbase = (w.p >> 8) << 8;                       // p = -1 gives -256: nothing staged
+    {
+      const int c = w.cbase >> 8;
+      const uint4 a = load_chunk(words, c, lane);
+      const uint4 b = load_chunk(words, c - 1, lane);
+      if (c >= 0) put_chunk(ring, c, lane, a);
+      if (c >= 1) put_chunk(ring, c - 1, lane, b);
+      w.pre = load_chunk(words, c - 2, lane);
+    }
+    __syncwarp();
+    w.rp = (w.p & (kRingWords - 1)) + kRingWords;
+
+    const int g_full = __reduce_min_sync(kFull, act);            // below it every coder has joined
+    const int steady_hi = min(g_full - 1, (hi1 >> 5) - 1);       // whole groups owned ...
+    // the previous entry of the same stream (there is one whenever lo > 0)
+    int act_p = -1, gtop_p = -1;
+    uint32_t x_p = 0;
+    if (lo > 0) {
+      act_p = ent[-1].act[lane];
+      x_p = ent[-1].x0[lane];
+      gtop_p = ent[-1].g_top;
+    }
+    sp.steady_lo = max((lo + kW - 1) >> 5, gtop_p + 1);          // ... fully decodable, above the check
+    sp.bad = false;
+    for (; g > steady_hi && g >= (lo >> 5); --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, sp.bad);
+    sp.g = g;
+    return true;
+  }
+
+  // One block of 8 steady group steps (the caller checks g - 7 >= steady_lo).
+  // 8 steps consume at most 256 words: with p >= cbase at the start of a
+  // block, every read stays inside the two staged chunks.
+  __device__ __forceinline__ void block(Walker& w, Span& sp) {
+    const int rp0 = w.rp;
+    const int i0 = sp.g * kW + lane;
+    typename SymOut<KIND>::T* o = out + (size_t)sp.g * kW + lane;
+    // adaptive: table numbers of the block after next into L1 (256 bytes, 8 per lane),
+    // only of groups this walk decodes (a shard plan stages no others)
+    if constexpr (is_adaptive<KIND>())
+      if (sp.g - 23 >= sp.steady_lo) prefetch_l1(tid + (sp.g - 23) * kW + lane * 8);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sstep(w, o - u * kW, i0 - u * kW);
+    sp.g -= 8;
+    settle(w, rp0);
+  }
+
+  // Two splits' blocks in lockstep, step by step: two independent chains of
+  // dependent table and word reads for the scheduler to overlap.
+  __device__ __forceinline__ void block2(Walker& w, Span& sp, EntryDecoder& B, Walker& wb, Span& sb) {
+    const int rp0 = w.rp, rpb0 = wb.rp;
+    const int i0 = sp.g * kW + lane, ib0 = sb.g * kW + lane;
+    typename SymOut<KIND>::T* o = out + (size_t)sp.g * kW + lane;
+    typename SymOut<KIND>::T* ob = B.out + (size_t)sb.g * kW + lane;
+    if constexpr (is_adaptive<KIND>()) {
+      if (sp.g - 23 >= sp.steady_lo) prefetch_l1(tid + (sp.g - 23) * kW + lane * 8);
+      if (sb.g - 23 >= sb.steady_lo) prefetch_l1(B.tid + (sb.g - 23) * kW + lane * 8);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      sstep(w, o - u * kW, i0 - u * kW);
+      B.sstep(wb, ob - u * kW, ib0 - u * kW);
+    }
+    sp.g -= 8;
+    sb.g -= 8;
+    settle(w, rp0);
+    B.settle(wb, rpb0);
+  }
+
+  // The rest of a walk: steady blocks, single steady steps, the predicated
+  // tail down to the owned low end, and the end checks.
+  __device__ __forceinline__ void finish(const DevEntry* __restrict__ ent, Walker& w, Span& sp, DevControl* ctl,
+                                         uint32_t entry_id) {
+    while (sp.g - 7 >= sp.steady_lo) block(w, sp);
+    int g = sp.g;
+    if (g >= sp.steady_lo) {
+      typename SymOut<KIND>::T* o = out + (size_t)g * kW + lane;
+      for (; g >= sp.steady_lo; --g) {
+        const int rp0 = w.rp;
+        sstep(w, o, g * kW + lane);
+        o -= kW;
+        settle(w, rp0);
+      }
+    }
+
+    // Reload what the tail needs instead of keeping it live across the steady
+    // loop (non-coherent loads the compiler cannot merge with the first ones).
+    const int lo = ld_keep(reinterpret_cast<const int*>(&ent->lo));
+    const int hi1 = ld_keep(reinterpret_cast<const int*>(&ent->hi1));
+    const int act = ld_keep(&ent->act[lane]);
+    const uint32_t x0 = (uint32_t)ld_keep(reinterpret_cast<const int*>(&ent->x0[lane]));
+    int act_p = -1;
+    uint32_t x_p = 0;
+    if (lo > 0) {
+      act_p = ld_keep(&ent[-1].act[lane]);
+      x_p = (uint32_t)ld_keep(reinterpret_cast<const int*>(&ent[-1].x0[lane]));
+    }
+    for (; g >= (lo >> 5); --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, sp.bad);
+
+    // The first thread of a stream must end where the encoder started (Eqs. 1-4 invert).
+    uint32_t err = 0;
+    if (w.p < -1) err |= kErrUnderrun;
+    if (lo == 0 && (w.p != -1 || __any_sync(kFull, w.x != kL))) err |= kErrCorrupt;
+    if (__any_sync(kFull, sp.bad)) err |= kErrCorrupt;
+    if (err && lane == 0) {
+      atomicOr(&ctl->errors, err);
+      atomicExch(&ctl->bad_entry, entry_id + 1);
+    }
+  }
+
+  // One split per warp (one coder lane per thread): the walk of begin and
+  // finish written as one function, which keeps fewer values live across
+  // the steady loop.
   __device__ void run(const DevEntry* __restrict__ ent, DevControl* ctl, uint32_t entry_id) {
     int lo = (int)ent->lo, hi1 = (int)ent->hi1;
     if (lo >= hi1) return;
@@ -398,6 +529,21 @@ struct EntryDecoder {
       atomicExch(&ctl->bad_entry, entry_id + 1);
     }
   }
+
+  // Two splits per warp (two coder lanes per thread, one of each split, each
+  // split with its own word ring): both synchronisation phases, then their
+  // steady blocks in lockstep while both have one, then each alone.
+  __device__ void run2(const DevEntry* __restrict__ ent, uint32_t entry_id, EntryDecoder& B,
+                       const DevEntry* __restrict__ entb, uint32_t entb_id, DevControl* ctl) {
+    Walker w, wb;
+    Span sp, sb;
+    const bool a = begin(ent, w, sp);
+    const bool b = B.begin(entb, wb, sb);
+    if (a && b)
+      while (sp.g - 7 >= sp.steady_lo && sb.g - 7 >= sb.steady_lo) block2(w, sp, B, wb, sb);
+    if (a) finish(ent, w, sp, ctl, entry_id);
+    if (b) B.finish(entb, wb, sb, ctl, entb_id);
+  }
 };
 
 // Blocks of WARPS warps; the second launch bound asks for enough resident
@@ -410,19 +556,32 @@ struct EntryDecoder {
 #ifndef RECOIL_RESIDENT_WARPS_ADAPTIVE
 #define RECOIL_RESIDENT_WARPS_ADAPTIVE 32
 #endif
-template <uint32_t KIND, int WARPS>
+// Two lanes a thread hold two walks' state: 32 warps (64 splits) per SM for
+// the static kinds, 24 warps (48 splits) for the adaptive ones.
+#ifndef RECOIL_RESIDENT_WARPS_TWO_LANES
+#define RECOIL_RESIDENT_WARPS_TWO_LANES 32
+#endif
+#ifndef RECOIL_RESIDENT_WARPS_TWO_LANES_ADAPTIVE
+#define RECOIL_RESIDENT_WARPS_TWO_LANES_ADAPTIVE 24
+#endif
+template <uint32_t KIND, int WARPS, int LANES>
 struct Residency {
-  static constexpr int kWarps = is_adaptive<KIND>() ? RECOIL_RESIDENT_WARPS_ADAPTIVE : RECOIL_RESIDENT_WARPS;
+  static constexpr int kWarps =
+      LANES == 2 ? (is_adaptive<KIND>() ? RECOIL_RESIDENT_WARPS_TWO_LANES_ADAPTIVE : RECOIL_RESIDENT_WARPS_TWO_LANES)
+                 : (is_adaptive<KIND>() ? RECOIL_RESIDENT_WARPS_ADAPTIVE : RECOIL_RESIDENT_WARPS);
   static constexpr int kWant = kWarps / WARPS;
   static constexpr int kMinBlocks = kWant < 1 ? 1 : (kWant > 32 ? 32 : kWant);
 };
 
-template <uint32_t KIND, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlocks)) decode_kernel(const LaunchArgs a) {
+// LANES coder lanes per thread: each warp decodes LANES splits at once, lane
+// j of each split on thread j, every split with its own word ring.
+template <uint32_t KIND, int WARPS, int LANES>
+__global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS, LANES>::kMinBlocks))
+    decode_kernel(const LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_item;
   const int warp = threadIdx.x >> 5;
-  uint16_t* ring = reinterpret_cast<uint16_t*>(smem + a.table_smem) + warp * kRingSlots;
+  uint16_t* ring = reinterpret_cast<uint16_t*>(smem + a.table_smem) + warp * LANES * kRingSlots;
 
   auto stage = [&](const DevStream& st) {
     const uint4* src = reinterpret_cast<const uint4*>(a.table_pool + st.table);
@@ -430,42 +589,57 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlock
     const uint32_t n16 = st.table_bytes >> 4;
     for (uint32_t k = threadIdx.x; k < n16; k += WARPS * 32) dst[k] = __ldg(src + k);
   };
-  auto decode_entry = [&](const DevStream& st, uint32_t entry) {
+  auto decoder = [&](EntryDecoder<KIND>& d, const DevStream& st, const DevEntry* ent, uint16_t* r) {
     // the entry's own stream: an item may span streams that share one table
-    const DevEntry* ent = a.entries + entry;
     const uint32_t sid = ent->stream;
-    EntryDecoder<KIND> d;
     d.T.bind(smem, st);
     d.words = a.word_pool + a.streams[sid].words;
     d.tid = reinterpret_cast<const uint8_t*>(a.word_pool + a.streams[sid].tid);
-    d.ring = ring;
+    d.ring = r;
     d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[sid]);
     d.n = st.n_bits;
     d.mask = (1u << st.n_bits) - 1u;
     d.gt = lanemask_gt();
     d.lane = threadIdx.x & 31;
-    d.run(ent, a.control, entry);
+  };
+  auto decode_entry = [&](const DevStream& st, uint32_t entry) {
+    EntryDecoder<KIND> d;
+    decoder(d, st, a.entries + entry, ring);
+    d.run(a.entries + entry, a.control, entry);
+  };
+  // two entries, one lane of each per thread
+  auto decode_pair = [&](const DevStream& st, uint32_t e0, uint32_t e1) {
+    EntryDecoder<KIND> d, db;
+    decoder(d, st, a.entries + e0, ring);
+    decoder(db, st, a.entries + e1, ring + kRingSlots);
+    d.run2(a.entries + e0, e0, db, a.entries + e1, e1, a.control);
   };
 
   if (a.warp_queue) {
     // one table for the whole launch, one entry per item: stage once, then
-    // every warp pops items on its own (no barrier between entries)
+    // every warp pops LANES items at a time on its own (no barrier between entries)
     const DevStream& st = a.streams[a.items[0].stream];
     stage(st);
     __syncthreads();
     for (;;) {
       uint32_t it = 0;
-      if ((threadIdx.x & 31) == 0) it = atomicAdd(&a.control->head[a.kind], 1u);
+      if ((threadIdx.x & 31) == 0) it = atomicAdd(&a.control->head[a.kind], (uint32_t)LANES);
       it = __shfl_sync(kFull, it, 0);
       if (it >= a.n_items) break;
+      if constexpr (LANES == 2) {
+        if (it + 1 < a.n_items) {
+          decode_pair(st, a.items[it].entry, a.items[it + 1].entry);
+          continue;
+        }
+      }
       decode_entry(st, a.items[it].entry);
     }
     return;
   }
 
-  // CTA items: up to WARPS entries of one stream (or of streams sharing one
-  // table); the table is restaged when the stream changes and the warps pop
-  // the item's entries from a shared counter
+  // CTA items: up to WARPS * LANES entries of one stream (or of streams
+  // sharing one table); the table is restaged when the stream changes and the
+  // warps pop the item's entries, LANES at a time, from a shared counter
   __shared__ uint32_t s_next;
   uint32_t staged = 0xffffffffu;
   uint32_t it = blockIdx.x;
@@ -486,9 +660,15 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlock
     }
     for (;;) {
       uint32_t k = 0;
-      if ((threadIdx.x & 31) == 0) k = atomicAdd(&s_next, 1u);
+      if ((threadIdx.x & 31) == 0) k = atomicAdd(&s_next, (uint32_t)LANES);
       k = __shfl_sync(kFull, k, 0);
       if (k >= item.count) break;
+      if constexpr (LANES == 2) {
+        if (k + 1 < item.count) {
+          decode_pair(st, item.entry + k, item.entry + k + 1);
+          continue;
+        }
+      }
       decode_entry(st, item.entry + k);
     }
     if (!a.persistent) break;
@@ -496,8 +676,8 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS>::kMinBlock
   }
 }
 
-size_t smem_bytes(uint32_t warps, uint32_t table_smem) {
-  return (size_t)table_smem + (size_t)warps * kRingSlots * sizeof(uint16_t);
+size_t smem_bytes(uint32_t warps, uint32_t lanes, uint32_t table_smem) {
+  return (size_t)table_smem + (size_t)warps * lanes * kRingSlots * sizeof(uint16_t);
 }
 
 // The dynamic shared memory a kernel may use is raised only when a launch
@@ -508,81 +688,97 @@ size_t smem_bytes(uint32_t warps, uint32_t table_smem) {
 // device reset drops the attribute, not this record).
 constexpr int kMaxDevices = 64;
 
-template <uint32_t KIND, int WARPS>
+template <uint32_t KIND, int WARPS, int LANES>
 cudaError_t allow_smem(size_t sm, bool force) {
   static std::atomic<int> allowed[kMaxDevices];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = -1;
   if (!force && dev >= 0 && allowed[dev].load(std::memory_order_relaxed) >= (int)sm) return cudaSuccess;
   const int want = dev >= 0 && !force ? std::max<int>((int)sm, allowed[dev].load(std::memory_order_relaxed)) : (int)sm;
-  const cudaError_t e = cudaFuncSetAttribute(decode_kernel<KIND, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  const cudaError_t e =
+      cudaFuncSetAttribute(decode_kernel<KIND, WARPS, LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
   if (e == cudaSuccess && dev >= 0) allowed[dev].store(want, std::memory_order_relaxed);
   return e;
 }
 
-template <uint32_t KIND, int WARPS>
+template <uint32_t KIND, int WARPS, int LANES>
 cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  const size_t sm = smem_bytes(WARPS, a.table_smem);
+  const size_t sm = smem_bytes(WARPS, LANES, a.table_smem);
   for (int attempt = 0; attempt < 2; attempt++) {
-    cudaError_t e = allow_smem<KIND, WARPS>(sm, attempt > 0);
+    cudaError_t e = allow_smem<KIND, WARPS, LANES>(sm, attempt > 0);
     if (e != cudaSuccess) return e;
-    decode_kernel<KIND, WARPS><<<grid, WARPS * 32, sm, s>>>(a);
+    decode_kernel<KIND, WARPS, LANES><<<grid, WARPS * 32, sm, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaErrorInvalidValue || attempt > 0) return e;
   }
   return cudaErrorInvalidValue;
 }
 
-template <uint32_t KIND, int WARPS>
+template <uint32_t KIND, int WARPS, int LANES>
 int occupancy_kw(uint32_t table_smem, int* out) {
-  const size_t sm = smem_bytes(WARPS, table_smem);
-  if (allow_smem<KIND, WARPS>(sm, false) != cudaSuccess) return -1;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS>, WARPS * 32, sm) == cudaSuccess ? 0 : -1;
+  const size_t sm = smem_bytes(WARPS, LANES, table_smem);
+  if (allow_smem<KIND, WARPS, LANES>(sm, false) != cudaSuccess) return -1;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS, LANES>, WARPS * 32, sm) ==
+                 cudaSuccess
+             ? 0
+             : -1;
 }
 
-// Static kinds come in every CTA size, adaptive kinds in 4, 8, 16 and 32 warps.
+// One lane a thread: static kinds in every CTA size, adaptive kinds in 4, 8,
+// 16 and 32 warps. Two lanes a thread: static kinds in 4, 8 and 16 warps,
+// adaptive kinds in 8, 16 and 24 warps.
+template <uint32_t KIND, typename F>
+auto by_shape(uint32_t warps, uint32_t lanes, F&& f) {
+  if (lanes == 2) {
+    if constexpr (is_adaptive<KIND>()) {
+      switch (warps) {
+        case 8: return f(std::integral_constant<int, 8>(), std::integral_constant<int, 2>());
+        case 16: return f(std::integral_constant<int, 16>(), std::integral_constant<int, 2>());
+        case 24: return f(std::integral_constant<int, 24>(), std::integral_constant<int, 2>());
+      }
+    } else {
+      switch (warps) {
+        case 4: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 2>());
+        case 8: return f(std::integral_constant<int, 8>(), std::integral_constant<int, 2>());
+        case 16: return f(std::integral_constant<int, 16>(), std::integral_constant<int, 2>());
+      }
+    }
+  } else if (lanes <= 1) {
+    if constexpr (is_adaptive<KIND>()) {
+      switch (warps) {
+        case 4: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 1>());
+        case 8: return f(std::integral_constant<int, 8>(), std::integral_constant<int, 1>());
+        case 16: return f(std::integral_constant<int, 16>(), std::integral_constant<int, 1>());
+        case 32: return f(std::integral_constant<int, 32>(), std::integral_constant<int, 1>());
+      }
+    } else {
+      switch (warps) {
+        case 1: return f(std::integral_constant<int, 1>(), std::integral_constant<int, 1>());
+        case 2: return f(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());
+        case 4: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 1>());
+        case 8: return f(std::integral_constant<int, 8>(), std::integral_constant<int, 1>());
+        case 16: return f(std::integral_constant<int, 16>(), std::integral_constant<int, 1>());
+        case 32: return f(std::integral_constant<int, 32>(), std::integral_constant<int, 1>());
+      }
+    }
+  }
+  return f(std::integral_constant<int, 0>(), std::integral_constant<int, 0>());
+}
+
 template <uint32_t KIND>
 cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  if constexpr (is_adaptive<KIND>()) {
-    switch (a.warps) {
-      case 4: return launch_kw<KIND, 4>(a, grid, s);
-      case 8: return launch_kw<KIND, 8>(a, grid, s);
-      case 16: return launch_kw<KIND, 16>(a, grid, s);
-      case 32: return launch_kw<KIND, 32>(a, grid, s);
-    }
-  } else {
-    switch (a.warps) {
-      case 1: return launch_kw<KIND, 1>(a, grid, s);
-      case 2: return launch_kw<KIND, 2>(a, grid, s);
-      case 4: return launch_kw<KIND, 4>(a, grid, s);
-      case 8: return launch_kw<KIND, 8>(a, grid, s);
-      case 16: return launch_kw<KIND, 16>(a, grid, s);
-      case 32: return launch_kw<KIND, 32>(a, grid, s);
-    }
-  }
-  return cudaErrorInvalidValue;
+  return by_shape<KIND>(a.warps, a.lanes, [&](auto w, auto l) -> cudaError_t {
+    if constexpr (decltype(w)::value == 0) return cudaErrorInvalidValue;
+    else return launch_kw<KIND, decltype(w)::value, decltype(l)::value>(a, grid, s);
+  });
 }
 
 template <uint32_t KIND>
-int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
-  if constexpr (is_adaptive<KIND>()) {
-    switch (warps) {
-      case 4: return occupancy_kw<KIND, 4>(table_smem, out);
-      case 8: return occupancy_kw<KIND, 8>(table_smem, out);
-      case 16: return occupancy_kw<KIND, 16>(table_smem, out);
-      case 32: return occupancy_kw<KIND, 32>(table_smem, out);
-    }
-  } else {
-    switch (warps) {
-      case 1: return occupancy_kw<KIND, 1>(table_smem, out);
-      case 2: return occupancy_kw<KIND, 2>(table_smem, out);
-      case 4: return occupancy_kw<KIND, 4>(table_smem, out);
-      case 8: return occupancy_kw<KIND, 8>(table_smem, out);
-      case 16: return occupancy_kw<KIND, 16>(table_smem, out);
-      case 32: return occupancy_kw<KIND, 32>(table_smem, out);
-    }
-  }
-  return -1;
+int occupancy_k(uint32_t warps, uint32_t lanes, uint32_t table_smem, int* out) {
+  return by_shape<KIND>(warps, lanes, [&](auto w, auto l) -> int {
+    if constexpr (decltype(w)::value == 0) return -1;
+    else return occupancy_kw<KIND, decltype(w)::value, decltype(l)::value>(table_smem, out);
+  });
 }
 
 }  // namespace
@@ -590,6 +786,12 @@ int occupancy_k(uint32_t warps, uint32_t table_smem, int* out) {
 bool warps_supported(uint32_t w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32; }
 
 bool adaptive_warps_supported(uint32_t w) { return w == 4 || w == 8 || w == 16 || w == 32; }
+
+bool shape_supported(bool adaptive, uint32_t warps, uint32_t lanes) {
+  if (lanes == 2) return adaptive ? (warps == 8 || warps == 16 || warps == 24) : (warps == 4 || warps == 8 || warps == 16);
+  if (lanes > 1) return false;
+  return adaptive ? adaptive_warps_supported(warps) : warps_supported(warps);
+}
 
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   switch (kind) {
@@ -605,16 +807,16 @@ cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cud
   return cudaErrorInvalidValue;
 }
 
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out) {
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t lanes, uint32_t table_smem, int* out) {
   switch (kind) {
-    case kPacked8: return occupancy_k<kPacked8>(warps, table_smem, out);
-    case kGeneric8: return occupancy_k<kGeneric8>(warps, table_smem, out);
-    case kGeneric16: return occupancy_k<kGeneric16>(warps, table_smem, out);
-    case kAdaptive8: return occupancy_k<kAdaptive8>(warps, table_smem, out);
-    case kAdaptive16: return occupancy_k<kAdaptive16>(warps, table_smem, out);
-    case kAdaptive16Wide: return occupancy_k<kAdaptive16Wide>(warps, table_smem, out);
-    case kAdaptive8Pair: return occupancy_k<kAdaptive8Pair>(warps, table_smem, out);
-    case kAdaptive16Pair: return occupancy_k<kAdaptive16Pair>(warps, table_smem, out);
+    case kPacked8: return occupancy_k<kPacked8>(warps, lanes, table_smem, out);
+    case kGeneric8: return occupancy_k<kGeneric8>(warps, lanes, table_smem, out);
+    case kGeneric16: return occupancy_k<kGeneric16>(warps, lanes, table_smem, out);
+    case kAdaptive8: return occupancy_k<kAdaptive8>(warps, lanes, table_smem, out);
+    case kAdaptive16: return occupancy_k<kAdaptive16>(warps, lanes, table_smem, out);
+    case kAdaptive16Wide: return occupancy_k<kAdaptive16Wide>(warps, lanes, table_smem, out);
+    case kAdaptive8Pair: return occupancy_k<kAdaptive8Pair>(warps, lanes, table_smem, out);
+    case kAdaptive16Pair: return occupancy_k<kAdaptive16Pair>(warps, lanes, table_smem, out);
   }
   return -1;
 }

@@ -146,20 +146,25 @@ struct LaunchArgs {
   uint32_t table_smem;       // bytes reserved for tables in shared memory
   uint32_t warps;            // warps per CTA
   uint32_t warp_queue;       // 1: every item is one entry and all share one table; warps pop items alone
+  uint32_t lanes;            // coder lanes a thread (splits a warp decodes at once): 1 (0 reads as 1) or 2
 };
 
 // Grid of a persistent launch: enough CTAs for the items, at most the resident ones.
 inline unsigned launch_grid(const LaunchArgs& a, int ctas_per_sm, int sms) {
-  const uint64_t need = a.warp_queue ? (a.n_items + a.warps - 1) / a.warps : a.n_items;
+  const uint64_t per_cta = (uint64_t)a.warps * (a.lanes > 1 ? a.lanes : 1);
+  const uint64_t need = a.warp_queue ? (a.n_items + per_cta - 1) / per_cta : a.n_items;
   const uint64_t cap = (uint64_t)ctas_per_sm * (uint64_t)sms;
   return (unsigned)(need < cap ? need : cap);
 }
 
 // Kernel launchers (decode_kernels.cu).
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s);
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t table_smem, int* out);
-size_t ring_smem_per_warp();
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t lanes, uint32_t table_smem, int* out);
+size_t ring_smem_per_warp();   // one split's word ring; a warp holds one per lane a thread
 bool warps_supported(uint32_t warps);   // CTA sizes the kernels are built for: 1, 2, 4, 8, 16, 32 warps
 bool adaptive_warps_supported(uint32_t warps);   // adaptive kinds: 4, 8, 16, 32 warps
+// CTA shapes built: one lane a thread as above; two lanes a thread: static
+// kinds 4, 8, 16 warps, adaptive kinds 8, 16, 24 warps
+bool shape_supported(bool adaptive, uint32_t warps, uint32_t lanes);
 
 }  // namespace recoil

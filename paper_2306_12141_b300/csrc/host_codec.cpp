@@ -67,6 +67,45 @@ const std::vector<uint32_t>& Stream::owned_ends() const {
   return owned_end;
 }
 
+// Sec. 3.3: the combined splits should own close symbol counts. For split k
+// the kept entry is the one whose owned end (smallest recorded index) lies
+// nearest to (k+1) N / Mp, searched after the previous kept entry and leaving
+// one entry for each later split (ties: the smaller end, then the earlier
+// entry); the final entry is always kept. Owned ends never decrease, so each
+// choice is a gallop from the previous pick and a binary search.
+void combine_picks(const Stream& in, uint32_t target, std::vector<uint32_t>& keep) {
+  keep.clear();
+  if (target < 1) target = 1;
+  const uint64_t R = in.entries.size();                     // regular entries
+  const uint64_t Mp = std::min<uint64_t>(target, R + 1);
+  const std::vector<uint32_t>& m = in.owned_ends();        // cached: serving combines per request
+  keep.reserve(Mp - 1);
+  uint64_t first = 0;
+  for (uint64_t k = 0; k + 1 < Mp; k++) {
+    const uint64_t last = R - (Mp - 1 - k);
+    const uint64_t t = (uint64_t)((unsigned __int128)(k + 1) * in.n_syms / Mp);
+    // the first end >= t in [first, last]: gallop from the previous pick
+    // (targets are about R / Mp entries apart), then bisect the last stride
+    uint64_t below = first, step = 1;
+    while (below + step <= last && m[below + step - 1] < t) {
+      below += step;
+      step *= 2;
+    }
+    const auto lo = m.begin() + first;
+    const uint64_t b = std::lower_bound(m.begin() + below, m.begin() + std::min(below + step, last + 1), t) - m.begin();
+    uint64_t pick;
+    if (b == first) {
+      pick = b;
+    } else {
+      const uint64_t a = m[b - 1];                                // the largest end below t
+      if (b <= last && m[b] - t < t - a) pick = b;
+      else pick = std::lower_bound(lo, m.begin() + b, (uint32_t)a) - m.begin();
+    }
+    keep.push_back((uint32_t)pick);
+    first = pick + 1;
+  }
+}
+
 // --------------------------------------------------------------- quantiser
 // Present symbols get max(1, round_half_even(c 2^n / N)); then the sum is
 // corrected to 2^n one unit at a time, cycling over present symbols in order
@@ -397,7 +436,6 @@ int recoil_encode_adaptive(const void* syms, uint64_t n_syms, const recoil_param
 int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_stream** out) {
   clear_error();
   if (!in || !out) return fail(RECOIL_EINVAL, "null argument");
-  if (target < 1) target = 1;
   *out = nullptr;
   try {
     std::unique_ptr<recoil_stream> s(new recoil_stream());
@@ -410,41 +448,14 @@ int recoil_combine_splits(const recoil_stream* in, uint32_t target, recoil_strea
     s->words = in->words;
     s->pinned_words = in->pinned_words;
     std::memcpy(s->final_x, in->final_x, sizeof s->final_x);
-    // Sec. 3.3: the combined splits should own close symbol counts. For split
-    // k the kept entry is the one whose owned end (smallest recorded index)
-    // lies nearest to (k+1) N / Mp, searched after the previous kept entry and
-    // leaving one entry for each later split (ties: the smaller end, then the
-    // earlier entry); the final entry is always kept. Owned ends never
-    // decrease, so each choice is a binary search.
-    const uint64_t R = in->entries.size();                    // regular entries
-    const uint64_t Mp = std::min<uint64_t>(target, R + 1);
-    const std::vector<uint32_t>& m = in->owned_ends();       // cached: serving combines per request
-    s->entries.reserve(Mp - 1);
-    s->owned_end.reserve(Mp - 1);
-    uint64_t first = 0;
-    for (uint64_t k = 0; k + 1 < Mp; k++) {
-      const uint64_t last = R - (Mp - 1 - k);
-      const uint64_t t = (uint64_t)((unsigned __int128)(k + 1) * in->n_syms / Mp);
-      // the first end >= t in [first, last]: gallop from the previous pick
-      // (targets are about R / Mp entries apart), then bisect the last stride
-      uint64_t below = first, step = 1;
-      while (below + step <= last && m[below + step - 1] < t) {
-        below += step;
-        step *= 2;
-      }
-      const auto lo = m.begin() + first;
-      const uint64_t b = std::lower_bound(m.begin() + below, m.begin() + std::min(below + step, last + 1), t) - m.begin();
-      uint64_t pick;
-      if (b == first) {
-        pick = b;
-      } else {
-        const uint64_t a = m[b - 1];                                // the largest end below t
-        if (b <= last && m[b] - t < t - a) pick = b;
-        else pick = std::lower_bound(lo, m.begin() + b, (uint32_t)a) - m.begin();
-      }
+    std::vector<uint32_t> keep;
+    combine_picks(*in, target, keep);
+    const std::vector<uint32_t>& m = in->owned_ends();
+    s->entries.reserve(keep.size());
+    s->owned_end.reserve(keep.size());
+    for (uint32_t pick : keep) {
       s->entries.push_back(in->entries[pick]);
       s->owned_end.push_back(m[pick]);
-      first = pick + 1;
     }
     s->owned_end_ready = true;
     *out = s.release();

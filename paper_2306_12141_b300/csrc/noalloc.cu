@@ -96,7 +96,7 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
   for (uint32_t k = 0; k < kKinds; k++) {
     if (!img.kind_count[k]) continue;
     const uint32_t smem = (uint32_t)((img.kind_smem[k] + 15) / 16 * 16);
-    if (occupancy_ctas_per_sm(k, img.warps, smem, &per_sm[k]) != 0 || per_sm[k] <= 0) {
+    if (occupancy_ctas_per_sm(k, img.warps, img.lanes, smem, &per_sm[k]) != 0 || per_sm[k] <= 0) {
       recoil_plan_free(plan);
       return fail(RECOIL_ECUDA, "occupancy query failed");
     }
@@ -120,6 +120,7 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
   a.outs = reinterpret_cast<void* const*>(scratch + img.off_outs);
   a.control = reinterpret_cast<DevControl*>(scratch);
   a.warps = img.warps;
+  a.lanes = img.lanes;
   const DevItem* items = reinterpret_cast<const DevItem*>(scratch + img.off_items);
   for (uint32_t k = 0; e == cudaSuccess && k < kKinds; k++) {
     if (!img.kind_count[k]) continue;

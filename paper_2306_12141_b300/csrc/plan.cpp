@@ -242,6 +242,7 @@ struct recoil_plan {
   std::vector<const Stream*> streams;
   recoil_batch_opts opts{};
   uint32_t warps = 16;
+  uint32_t lanes = 1;                                  // coder lanes a thread (splits a warp decodes at once)
 
   std::vector<uint8_t> meta;                           // control .. entries
   std::vector<uint8_t> tables;
@@ -287,7 +288,7 @@ static int device_sms();
 // CTAs of `warps` warps that one SM holds when each needs `smem` bytes of
 // shared memory; adaptive kernels are built for 32 resident warps an SM
 // (64 registers a thread).
-static uint64_t adaptive_ctas_per_sm(uint32_t warps, size_t smem) {
+static uint64_t adaptive_ctas_per_sm(uint32_t warps, uint32_t lanes, size_t smem) {
   int dev = 0, per_sm = 0, reserved = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
@@ -297,7 +298,8 @@ static uint64_t adaptive_ctas_per_sm(uint32_t warps, size_t smem) {
     per_sm = 228 * 1024;                           // sm_100 / sm_103
     reserved = 1024;
   }
-  return std::min<uint64_t>((uint64_t)per_sm / (smem + (size_t)reserved), 32 / warps);
+  // registers: 32 warps an SM with one lane a thread, 24 with two
+  return std::min<uint64_t>((uint64_t)per_sm / (smem + (size_t)reserved), (lanes == 2 ? 24 : 32) / warps);
 }
 
 // Guide width of each adaptive kind in a plan: 2^10 buckets (about a third
@@ -325,7 +327,8 @@ static void choose_guides(const recoil_plan* P, uint32_t* guide) {
     paired[k] = std::max(paired[k], bytes);
     pairable[k] = pairable[k] && bytes > 0;
   }
-  const size_t rings = (size_t)P->warps * ring_smem_per_warp() + 16;
+  const size_t rings = (size_t)P->warps * P->lanes * ring_smem_per_warp() + 16;
+  const uint64_t per_cta = (uint64_t)P->warps * P->lanes;   // splits a CTA decodes at once
   const uint64_t sms = (uint64_t)device_sms();
   for (uint32_t k = 0; k < kKinds; k++) {
     if (!entries[k]) continue;
@@ -335,16 +338,18 @@ static void choose_guides(const recoil_plan* P, uint32_t* guide) {
     }
     // the variant that keeps the most splits resident; on a tie the finer
     // guide, and the paired layout before either
-    uint64_t best = std::min(entries[k], adaptive_ctas_per_sm(P->warps, coarse[k] + rings) * sms * P->warps);
+    uint64_t best = std::min(entries[k], adaptive_ctas_per_sm(P->warps, P->lanes, coarse[k] + rings) * sms * per_cta);
     if (fine[k] + rings <= kMaxSmem) {
-      const uint64_t cap10 = std::min(entries[k], adaptive_ctas_per_sm(P->warps, fine[k] + rings) * sms * P->warps);
+      const uint64_t cap10 =
+          std::min(entries[k], adaptive_ctas_per_sm(P->warps, P->lanes, fine[k] + rings) * sms * per_cta);
       if (cap10 >= best) {
         guide[k] = kGuideBitsFine;
         best = cap10;
       }
     }
     if (pairable[k] && !(P->opts.flags & RECOIL_BATCH_NO_PAIRS) && paired[k] + rings <= kMaxSmem) {
-      const uint64_t capp = std::min(entries[k], adaptive_ctas_per_sm(P->warps, paired[k] + rings) * sms * P->warps);
+      const uint64_t capp =
+          std::min(entries[k], adaptive_ctas_per_sm(P->warps, P->lanes, paired[k] + rings) * sms * per_cta);
       if (capp >= best) guide[k] = kGuidePairs;
     }
   }
@@ -355,8 +360,10 @@ static int plan_build(recoil_plan* P) {
   const bool per_stream = P->opts.flags & RECOIL_BATCH_PER_STREAM;
   const uint32_t warps = P->warps;
   for (const Stream* s : P->streams)
-    if (s->adaptive() && !adaptive_warps_supported(warps))
-      return fail(RECOIL_EINVAL, "adaptive streams decode with 4, 8, 16 or 32 warps per CTA");
+    if (!shape_supported(s->adaptive(), warps, P->lanes))
+      return fail(RECOIL_EINVAL, P->lanes == 2 ? (s->adaptive() ? "two lanes a thread: adaptive streams decode with 8, 16 or 24 warps per CTA"
+                                                                : "two lanes a thread: static streams decode with 4, 8 or 16 warps per CTA")
+                                               : "adaptive streams decode with 4, 8, 16 or 32 warps per CTA");
   uint32_t guide[kKinds];
   choose_guides(P, guide);
   std::vector<DevStream> ds(count);
@@ -474,7 +481,7 @@ static int plan_build(recoil_plan* P) {
     size_t e = first + (P->shard ? P->entry_first : 0);
     // items of one CTA round: longer items (several rounds) leave longer tails
     // at the end of the queue and measured much slower on uneven batches
-    const uint32_t cap = warps;
+    const uint32_t cap = warps * P->lanes;
     if (same_table && !P->shard && items.back().it.count < cap) {
       const uint32_t take = (uint32_t)std::min<size_t>(cap - items.back().it.count, end_e - e);
       items.back().it.count += take;
@@ -493,7 +500,7 @@ static int plan_build(recoil_plan* P) {
     }
   }
   for (uint32_t k = 0; k < kKinds; k++) {
-    if (P->kind_smem[k] + warps * ring_smem_per_warp() > kMaxSmem)
+    if (P->kind_smem[k] + warps * P->lanes * ring_smem_per_warp() > kMaxSmem)
       return fail(RECOIL_EINVAL, "decoder tables too large for shared memory (alphabet or n too large)");
   }
   // Kinds whose items all decode with one table (one stream, or streams with
@@ -581,6 +588,7 @@ void plan_image(const recoil_plan* P, PlanImage* o) {
   o->table_bytes = P->tables.size();
   o->ws_off_tables = P->off_tables;
   o->warps = P->warps;
+  o->lanes = P->lanes;
   for (uint32_t k = 0; k < kKinds; k++) {
     o->kind_first[k] = P->kind_first[k];
     o->kind_count[k] = P->kind_count[k];
@@ -608,12 +616,17 @@ static int device_sms() {
 // 2368 and more within 1% of the best size. Adaptive streams with 64 or more
 // splits an SM take 32-warp CTAs, one per SM, which leaves room for the finer
 // guide (adaptive latents at 9472 splits: 1000 against 945 GB/s).
-static uint32_t auto_warps(uint64_t splits, bool adaptive) {
-  const uint64_t per_sm = splits / (uint64_t)device_sms();
-  if (adaptive && per_sm >= 64) return 32;
-  uint32_t w = 4;
+static uint32_t auto_warps(uint64_t splits, bool adaptive, uint32_t lanes) {
+  const uint64_t per_sm = splits / lanes / (uint64_t)device_sms();   // warps' worth of splits an SM
+  if (adaptive && per_sm >= 64 / lanes) return lanes == 2 ? 24 : 32;
+  uint32_t w = adaptive && lanes == 2 ? 8 : 4;
   while (w < 16 && (uint64_t)w * 2 <= per_sm) w *= 2;
   return w;
+}
+
+// CTA sizes some kernel exists for (per kind checked by shape_supported).
+static bool shape_warps_ok(uint32_t warps, uint32_t lanes) {
+  return lanes == 2 ? (warps == 4 || warps == 8 || warps == 16 || warps == 24) : warps_supported(warps);
 }
 
 static int cuda_fail(cudaError_t e, const char* what) {
@@ -696,6 +709,7 @@ static int plan_launch(recoil_plan* P, cudaStream_t cs) {
   a.outs = reinterpret_cast<void* const*>(meta + P->off_outs);
   a.control = ctl;
   a.warps = P->warps;
+  a.lanes = P->lanes;
   const DevItem* items = reinterpret_cast<const DevItem*>(meta + P->off_items);
   if (P->opts.flags & RECOIL_BATCH_PER_STREAM) {
     for (size_t s = 0; s < P->streams.size(); s++) {
@@ -721,7 +735,7 @@ static int plan_launch(recoil_plan* P, cudaStream_t cs) {
     a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
     a.warp_queue = P->kind_warp_queue[k];
     int per_sm = (int)P->opts.ctas_per_sm;
-    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, a.table_smem, &per_sm) != 0)
+    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, P->lanes, a.table_smem, &per_sm) != 0)
       return fail(RECOIL_ECUDA, "occupancy query failed");
     if (per_sm <= 0) return fail(RECOIL_EINVAL, "kernel does not fit on an SM with these options");
     const unsigned grid = launch_grid(a, per_sm, P->sms);
@@ -743,6 +757,7 @@ int recoil_plan_create(const recoil_stream* const* streams, uint32_t count, cons
     std::unique_ptr<recoil_plan> P(new recoil_plan());
     if (opts) P->opts = *opts;
     P->warps = P->opts.warps_per_cta;
+    P->lanes = (P->opts.flags & RECOIL_BATCH_TWO_LANES) ? 2 : 1;
     if (!P->warps) {
       uint64_t splits = 0;
       bool adaptive = count > 0;
@@ -753,9 +768,11 @@ int recoil_plan_create(const recoil_stream* const* streams, uint32_t count, cons
                       : streams[i]->entries.size() + 1;
         adaptive = adaptive && streams[i]->adaptive();
       }
-      P->warps = auto_warps(splits, adaptive);
+      P->warps = auto_warps(splits, adaptive, P->lanes);
     }
-    if (!warps_supported(P->warps)) return fail(RECOIL_EINVAL, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
+    if (!shape_warps_ok(P->warps, P->lanes))
+      return fail(RECOIL_EINVAL, P->lanes == 2 ? "two lanes a thread: warps_per_cta must be 4, 8, 16 or 24"
+                                               : "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
     for (uint32_t i = 0; i < count; i++) {
       if (!streams[i]) return fail(RECOIL_EINVAL, "null stream");
       const recoil_stream* s = streams[i];
@@ -763,7 +780,8 @@ int recoil_plan_create(const recoil_stream* const* streams, uint32_t count, cons
         // about split_symbols per split, rounded up to whole CTAs so that every
         // work item keeps all its warps busy on splits of equal size
         uint64_t want = std::max<uint64_t>(1, (s->n_syms + P->opts.split_symbols - 1) / P->opts.split_symbols);
-        want = (want + P->warps - 1) / P->warps * P->warps;
+        const uint64_t per_cta = (uint64_t)P->warps * P->lanes;
+        want = (want + per_cta - 1) / per_cta * per_cta;
         recoil_stream* c = nullptr;
         int rc = recoil_combine_splits(s, (uint32_t)std::min<uint64_t>(want, 0xffffffffu), &c);
         if (rc) return rc;
@@ -939,8 +957,12 @@ int recoil_plan_create_shard(const recoil_stream* s, uint32_t world, uint32_t ra
     if (first >= last) *sym_hi = *sym_lo;
     std::unique_ptr<recoil_plan> P(new recoil_plan());
     if (opts) P->opts = *opts;
-    P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta : auto_warps(std::max(first, last) - first, s->adaptive());
-    if (!warps_supported(P->warps)) return fail(RECOIL_EINVAL, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
+    P->lanes = (P->opts.flags & RECOIL_BATCH_TWO_LANES) ? 2 : 1;
+    P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta
+                                     : auto_warps(std::max(first, last) - first, s->adaptive(), P->lanes);
+    if (!shape_warps_ok(P->warps, P->lanes))
+      return fail(RECOIL_EINVAL, P->lanes == 2 ? "two lanes a thread: warps_per_cta must be 4, 8, 16 or 24"
+                                               : "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
     P->streams.push_back(s);
     P->shard = true;
     P->entry_first = first;

@@ -52,6 +52,10 @@ struct Stream {
   const std::vector<uint32_t>& owned_ends() const; // owned_end, built on first use (entries never change)
 };
 
+// Regular entries of `in` kept when combining it to `target` splits
+// (recoil_combine_splits' rule; the final entry is always kept besides them).
+void combine_picks(const Stream& in, uint32_t target, std::vector<uint32_t>& keep);
+
 // Host images of a plan (plan.cpp), for entry points that place them in
 // device memory of their own. meta = control, output pointers, stream
 // descriptors, items, entries (offsets relative to meta); tables separate.
@@ -63,6 +67,7 @@ struct PlanImage {
   size_t table_bytes;
   size_t ws_off_tables;      // workspace offset of the tables (words start at 0)
   uint32_t warps;
+  uint32_t lanes;            // coder lanes a thread
   uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds], kind_warp_queue[kKinds];
 };
 }  // namespace recoil

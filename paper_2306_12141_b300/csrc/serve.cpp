@@ -8,7 +8,8 @@
 //     a launch slot allow, up to max_batch per launch,
 //   - combines each admitted stream to its share of the warp slots that are
 //     free at that moment (Sec. 3.3: the decoder's parallelism decides the
-//     split count), builds the split descriptors on the host, copies them to
+//     split count) by picking entries of the pool stream, whose descriptors
+//     are built once for the whole pool before the run, copies them to
 //     the slot's descriptor area and launches one persistent decode for the
 //     whole admission on the slot's own CUDA stream,
 // so requests that arrive while others run are admitted as memory and slots
@@ -162,7 +163,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   if (e != cudaSuccess) return fail(RECOIL_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
   int per_sm[kKinds] = {};
   for (uint32_t k = 0; k < kKinds; k++)
-    if (occupancy_ctas_per_sm(k, warps, kind_smem[k], &per_sm[k]) != 0 || per_sm[k] <= 0) per_sm[k] = 1;
+    if (occupancy_ctas_per_sm(k, warps, 1, kind_smem[k], &per_sm[k]) != 0 || per_sm[k] <= 0) per_sm[k] = 1;
   const uint32_t total_warps = (uint32_t)(per_sm[kPacked8] * sms) * warps;
 
   std::vector<Slot> slots(nslots);
@@ -202,6 +203,16 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
     }
   }
 
+  // every entry descriptor of every pool stream, built once like the resident
+  // words (a server prepares its content before it takes requests)
+  std::vector<std::vector<DevEntry>> pool_ents(pool_count);
+  try {
+    for (uint32_t i = 0; i < pool_count; i++) build_entries(*pool[i], 0, pool_ents[i]);
+  } catch (const std::bad_alloc&) {
+    cleanup();
+    return fail(RECOIL_ENOMEM, "host allocation failed");
+  }
+
   // the run clock: host t0 and a device event recorded at the same moment
   e = cudaEventRecord(t0ev, slots[0].stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(t0ev);
@@ -210,9 +221,17 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   uint32_t warps_busy = 0;
   double first_arrival = n_req ? req_arrival_s[0] : 0.0, last_done = 0.0;
   uint64_t sym_bytes_total = 0;
-  std::vector<DevEntry> ents;
+  // an admitted split: its descriptor in the pool set, its owned low end and
+  // its request's place in the launch
+  struct EntRef {
+    const DevEntry* src;
+    uint32_t lo;
+    uint32_t stream;
+  };
+  std::vector<EntRef> ents;
   std::vector<DevItem> items;
   std::vector<uint32_t> item_kind;
+  std::vector<uint32_t> keep;
   int status = RECOIL_OK;
 
   while (done < n_req && e == cudaSuccess && status == RECOIL_OK) {
@@ -305,14 +324,18 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
             want = (want + warps - 1) / warps * warps;
             target = (uint32_t)std::min<uint64_t>(target, want);
           }
-          recoil_stream* c = nullptr;
-          if (recoil_combine_splits(src, target, &c) != RECOIL_OK) {
-            status = RECOIL_ENOMEM;
-            break;
-          }
-          std::unique_ptr<recoil_stream> cg(c);
+          // combine (Sec. 3.3) without building a combined stream: the kept
+          // entries' descriptors come from the pool stream's full set, each
+          // owning from the previous kept entry's end
+          const std::vector<DevEntry>& full = pool_ents[req_stream[r]];
+          combine_picks(*src, target, keep);
           const size_t first = ents.size();
-          build_entries(*c, (uint32_t)k, ents);
+          uint32_t prev_end = 0;
+          for (uint32_t pick : keep) {
+            ents.push_back(EntRef{&full[pick], prev_end, (uint32_t)k});
+            prev_end = full[pick].hi1;
+          }
+          ents.push_back(EntRef{&full.back(), prev_end, (uint32_t)k});   // the final-state entry
           results[r].splits = (uint32_t)(ents.size() - first);
           results[r].launch = launches;
           ds[k] = pool_ds[req_stream[r]];
@@ -322,7 +345,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
             it.stream = (uint32_t)k;
             it.entry = (uint32_t)x;
             it.count = (uint32_t)std::min<size_t>(warps, ents.size() - x);
-            it.work = (uint32_t)std::min<uint64_t>(c->n_syms / std::max<size_t>(1, c->entries.size() + 1), 0x7fffffff);
+            it.work = (uint32_t)std::min<uint64_t>(src->n_syms / (keep.size() + 1), 0x7fffffff);
             items.push_back(it);
             item_kind.push_back(ds[k].kind);
           }
@@ -353,7 +376,12 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
           if (!kind_count[k]) kind_first[k] = x;
           kind_count[k]++;
         }
-        std::memcpy(h + off_entries, ents.data(), ents.size() * sizeof(DevEntry));
+        DevEntry* he = reinterpret_cast<DevEntry*>(h + off_entries);
+        for (size_t x = 0; x < ents.size(); x++) {             // one copy, pool descriptor to staging
+          he[x] = *ents[x].src;
+          he[x].lo = ents[x].lo;
+          he[x].stream = ents[x].stream;
+        }
         e = cudaMemcpyAsync(sl.dev, h, meta_bytes, cudaMemcpyHostToDevice, sl.stream);
         LaunchArgs a{};
         a.streams = reinterpret_cast<const DevStream*>(sl.dev + off_streams);

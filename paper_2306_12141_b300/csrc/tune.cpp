@@ -1,5 +1,6 @@
-// Autotuner for batched decoding: picks warps per CTA and the split size a
-// batch is combined to by timing each candidate on the caller's own streams.
+// Autotuner for batched decoding: picks coder lanes a thread (one split a
+// warp, or two in lockstep), warps per CTA and the split size a batch is
+// combined to by timing each candidate on the caller's own streams.
 //
 // Candidates differ only in how streams are split, so they share the bulk of
 // the device image (words and tables): it is uploaded once and each candidate
@@ -20,21 +21,27 @@
 namespace recoil {
 namespace {
 
-const uint32_t kWarps[] = {4, 8, 16, 32};
+const uint32_t kWarps[] = {4, 8, 16, 24, 32};
 const uint32_t kSplit[] = {32768, 65536, 131072, 262144};
 
-// Candidate options: warps x split sizes, or warps alone on the streams' own
-// splits. 32-warp CTAs only for adaptive streams (one CTA an SM leaves room
-// for the finer guide); static kinds keep 4 to 16.
-std::vector<recoil_batch_opts> candidates(bool keep_splits, bool adaptive) {
+// Candidate options: lanes a thread (1 or 2) x warps x split sizes, or lanes
+// x warps alone on the streams' own splits, every shape a kernel is built for
+// with each kind in the batch. 32-warp CTAs only for adaptive streams (one
+// CTA an SM leaves room for the finer guide); static kinds keep 4 to 16.
+std::vector<recoil_batch_opts> candidates(bool keep_splits, bool has_static, bool has_adaptive) {
   std::vector<recoil_batch_opts> c;
-  for (uint32_t w : kWarps) {
-    if (w == 32 && !adaptive) continue;
-    if (keep_splits) {
-      c.push_back(recoil_batch_opts{w, 0, 0, 0});
-      continue;
+  for (uint32_t lanes : {1u, 2u}) {
+    for (uint32_t w : kWarps) {
+      if (has_static && !shape_supported(false, w, lanes)) continue;
+      if (has_adaptive && !shape_supported(true, w, lanes)) continue;
+      if (lanes == 1 && w == 32 && !has_adaptive) continue;
+      const uint32_t flags = lanes == 2 ? RECOIL_BATCH_TWO_LANES : 0;
+      if (keep_splits) {
+        c.push_back(recoil_batch_opts{w, 0, 0, flags});
+        continue;
+      }
+      for (uint32_t sp : kSplit) c.push_back(recoil_batch_opts{w, 0, sp, flags});
     }
-    for (uint32_t sp : kSplit) c.push_back(recoil_batch_opts{w, 0, sp, 0});
   }
   return c;
 }
@@ -61,6 +68,7 @@ std::string tune_key(const recoil_stream* const* s, uint32_t count) {
   return k.str();
 }
 
+// Cache lines: key, warps, split symbols, lanes a thread, time (ms).
 bool cache_lookup(const char* path, const std::string& key, recoil_batch_opts* best, float* ms) {
   if (!path) return false;
   std::ifstream f(path);
@@ -69,11 +77,11 @@ bool cache_lookup(const char* path, const std::string& key, recoil_batch_opts* b
   while (std::getline(f, line)) {
     std::istringstream in(line);
     std::string k;
-    uint32_t w = 0, sp = 0;
+    uint32_t w = 0, sp = 0, lanes = 0;
     float t = 0;
-    if (in >> k >> w >> sp >> t && k == key && warps_supported(w)) {
-      best->warps_per_cta = w;
-      best->split_symbols = sp;
+    if (in >> k >> w >> sp >> lanes >> t && k == key && (lanes == 1 || lanes == 2) &&
+        (lanes == 2 ? (w == 4 || w == 8 || w == 16 || w == 24) : warps_supported(w))) {
+      *best = recoil_batch_opts{w, 0, sp, lanes == 2 ? RECOIL_BATCH_TWO_LANES : 0u};
       *ms = t;
       hit = true;                          // the last line for a key wins
     }
@@ -84,7 +92,8 @@ bool cache_lookup(const char* path, const std::string& key, recoil_batch_opts* b
 void cache_store(const char* path, const std::string& key, const recoil_batch_opts& b, float ms) {
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << ' ' << b.warps_per_cta << ' ' << b.split_symbols << ' ' << ms << '\n';
+  f << key << ' ' << b.warps_per_cta << ' ' << b.split_symbols << ' '
+    << ((b.flags & RECOIL_BATCH_TWO_LANES) ? 2 : 1) << ' ' << ms << '\n';
 }
 
 struct Candidate {
@@ -95,6 +104,12 @@ struct Candidate {
 bool any_adaptive(const recoil_stream* const* s, uint32_t count) {
   for (uint32_t i = 0; i < count; i++)
     if (s && s[i] && s[i]->adaptive()) return true;
+  return false;
+}
+
+bool any_static(const recoil_stream* const* s, uint32_t count) {
+  for (uint32_t i = 0; i < count; i++)
+    if (s && s[i] && !s[i]->adaptive()) return true;
   return false;
 }
 
@@ -110,7 +125,7 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
   if (!bytes) return fail(RECOIL_EINVAL, "null argument");
   size_t mx = 0;
   for (bool keep : {false, true})
-    for (recoil_batch_opts o : candidates(keep, any_adaptive(streams, count))) {
+    for (recoil_batch_opts o : candidates(keep, any_static(streams, count), any_adaptive(streams, count))) {
       size_t b = 0;
       int rc = recoil_workspace_size(streams, count, &o, &b);
       if (rc) return rc;
@@ -143,7 +158,7 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
     for (Candidate& c : cands) recoil_plan_free(c.plan);
   };
   size_t bulk = 0;
-  for (const recoil_batch_opts& o : candidates(keep, any_adaptive(streams, count))) {
+  for (const recoil_batch_opts& o : candidates(keep, any_static(streams, count), any_adaptive(streams, count))) {
     Candidate c;
     c.opts = o;
     int rc = recoil_plan_create(streams, count, &c.opts, &c.plan);

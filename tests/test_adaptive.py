@@ -102,6 +102,10 @@ def test_adaptive_rejected_by_noalloc_and_small_ctas(recoil_lib):
     for w in (1, 2):
         with pytest.raises(R.RecoilError):
             R.Plan([p], {"warps_per_cta": w})
+    for w in (4, 32):                             # two lanes a thread: 8, 16 or 24 warps
+        with pytest.raises(R.RecoilError):
+            R.Plan([p], {"warps_per_cta": w, "flags": R.BATCH_TWO_LANES})
+    assert R.Plan([p], {"warps_per_cta": 24, "flags": R.BATCH_TWO_LANES}).warps_per_cta == 24
 
 
 def test_adaptive_plan_rejects_rows_beyond_shared_memory(recoil_lib):
@@ -208,6 +212,23 @@ def test_gpu_adaptive_cta_sizes_and_graph(recoil_lib, warps):
                                                                          "split_symbols": 20000}):
         (out,) = _gpu_decode(R, [p], opts)
         assert np.array_equal(out, s), opts
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cfg", CASES, ids=lambda c: f"n{c['n_bits']}_A{c['alphabet']}_T{c['n_tables']}")
+@pytest.mark.parametrize("warps", [8, 24])
+def test_gpu_adaptive_two_lanes_per_thread(recoil_lib, cfg, warps):
+    """Two coder lanes a thread for adaptive streams (8, 16 or 24 warps per CTA): every
+    layout the plan stages, at even and odd split counts, against the oracle."""
+    R = recoil_lib
+    a, tables, s, tid = _case(300_007, 31, **cfg)
+    p = R.encode_adaptive(s, cfg["n_bits"], tables, tid, 300)
+    o = oracle.encode_adaptive_with_splits(s, tid, tables, cfg["n_bits"], 300)
+    for flags in (R.BATCH_TWO_LANES, R.BATCH_TWO_LANES | R.BATCH_NO_PAIRS | R.BATCH_GRAPH):
+        for Mp in (300, 51):
+            (out,) = _gpu_decode(R, [R.combine_splits(p, Mp)], {"warps_per_cta": warps, "flags": flags})
+            assert np.array_equal(out, s), (flags, Mp)
+            assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(out.dtype)), (flags, Mp)
 
 
 @pytest.mark.gpu

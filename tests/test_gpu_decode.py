@@ -169,6 +169,51 @@ def test_batch_of_uneven_streams(recoil_lib, opts):
         assert np.array_equal(out, s)
 
 
+@pytest.mark.parametrize("opts", [
+    {"warps_per_cta": 4, "flags": 16},
+    {"warps_per_cta": 8, "flags": 16 | 4},       # two lanes a thread, graph replay
+    {"warps_per_cta": 16, "flags": 16, "split_symbols": 16384},
+    {"warps_per_cta": 8, "flags": 16 | 1},       # two lanes, one launch per stream
+    {"flags": 16},                               # two lanes, automatic CTA size
+])
+def test_batch_two_lanes_per_thread(recoil_lib, opts):
+    """Two coder lanes a thread (RECOIL_BATCH_TWO_LANES): each warp decodes two splits in
+    lockstep, one coder of each per thread; uneven batches of every static kind, with odd
+    item counts (a warp left with one split) and empty streams, decode exactly."""
+    R = recoil_lib
+    syms, streams = _batch_streams(R)
+    outs = gpu_decode(R, streams, opts)
+    for s, out in zip(syms, outs):
+        assert np.array_equal(out, s)
+
+
+@pytest.mark.parametrize("dist,params,n,sb", DISTS[:5])
+@pytest.mark.parametrize("warps", [4, 16])
+def test_two_lanes_single_stream_against_oracle(recoil_lib, dist, params, n, sb, warps):
+    """One stream (the warp-queue launch: warps pop two splits at a time) at several combined
+    counts, odd ones included, against the input and the oracle's split decode."""
+    R = recoil_lib
+    s = workloads.Stream("t", 200_003, sb, n, dist, params, seed=33).symbols()
+    p = R.encode_with_splits(s, n, 300)
+    o = oracle.encode_with_splits(s, n, 300)
+    for Mp in (300, 77, 2, 1):
+        c = R.combine_splits(p, Mp)
+        plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_TWO_LANES})
+        assert plan.warps_per_cta == warps
+        (out,) = gpu_decode(R, [c], {"warps_per_cta": warps, "flags": R.BATCH_TWO_LANES})
+        assert np.array_equal(out, s), Mp
+        assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(out.dtype)), Mp
+
+
+def test_two_lanes_rejects_unbuilt_shapes(recoil_lib):
+    R = recoil_lib
+    s = workloads.Stream("t", 10_000, 1, 12, "zipf", {"s": 1.2}, seed=3).symbols()
+    p = R.encode_with_splits(s, 12, 8)
+    for w in (1, 2, 32, 24):
+        with pytest.raises(R.RecoilError):
+            R.Plan([p], {"warps_per_cta": w, "flags": R.BATCH_TWO_LANES})
+
+
 def test_batch_graph_replay_and_new_outputs(recoil_lib):
     R = recoil_lib
     syms, streams = _batch_streams(R, count=30, seed=41)
