@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--streams", type=int, default=workloads.BATCH_STREAMS)
     ap.add_argument("--scale", type=float, default=1.0, help="shrink stream sizes (testing only)")
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2],
+                    help="coder lanes a thread (0: the autotuner's choice where it runs, else 1)")
     ap.add_argument("--split-symbols", type=int, default=-1)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--per-stream-steps", type=int, default=3)
@@ -379,11 +381,12 @@ def run_conventional(a):
     with ThreadPoolExecutor(max(1, min(64, os.cpu_count() or 1))) as ex:
         conv = list(ex.map(lambda p: R.encode_with_table(p, st.n_bits, freq, 1), parts))
     warps = a.warps or 16
+    lane_flag = R.BATCH_TWO_LANES if a.lanes == 2 else 0
     cs = torch.cuda.Stream(device=dev)
     ref = torch.from_numpy(s).to(dev)
     res = {}
     for name, streams in (("recoil", [rec]), ("conventional", conv)):
-        plan = R.Plan(streams, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+        plan = R.Plan(streams, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag})
         ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
         out = torch.empty(len(s), dtype=torch.uint8, device=dev)
         if name == "recoil":
@@ -473,6 +476,7 @@ def run_adaptive(a):
     s, tid = st.draw()
     enc = R.encode_adaptive(s, st.n_bits, tables, tid, max(1, min(65536, len(s) // 4096)))
     warps = a.warps                                    # 0: the library picks the CTA size
+    lane_flag = R.BATCH_TWO_LANES if a.lanes == 2 else 0
     cs = torch.cuda.Stream(device=dev)
     out = torch.empty(len(s) * 2, dtype=torch.uint8, device=dev)
     ref = torch.from_numpy(s.view(np.uint8)).to(dev)
@@ -493,7 +497,7 @@ def run_adaptive(a):
     sweep = {}
     with torch.cuda.stream(cs):
         for k in a.sweep:
-            sp = R.Plan([R.combine_splits(enc, k)], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+            sp = R.Plan([R.combine_splits(enc, k)], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag})
             sws = torch.empty(sp.workspace_size, dtype=torch.uint8, device=dev)
             sp.upload(sws, stream=cs)
             t = timed(lambda: sp.decode([out.data_ptr()], cs), 5, 2)
@@ -507,9 +511,10 @@ def run_adaptive(a):
             tws = torch.empty(R.autotune_workspace_size([c]), dtype=torch.uint8, device=dev)
             best, tms = R.autotune([c], [out.data_ptr()], tws, tws.numel(), cs, steps=3, keep_splits=True)
             warps = best["warps_per_cta"]
-            tuned = {"warps_per_cta": warps, "ms": round(tms, 4)}
+            lane_flag = best["flags"] & R.BATCH_TWO_LANES
+            tuned = {"warps_per_cta": warps, "lanes_per_thread": 2 if lane_flag else 1, "ms": round(tms, 4)}
             del tws
-        plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+        plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag})
         warps = plan.warps_per_cta
         ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
         plan.upload(ws, stream=cs)
@@ -528,7 +533,8 @@ def run_adaptive(a):
         e2e = None
         if not a.no_e2e:
             R.stream_pin(c)
-            pipe = R.Pipeline([c], {"warps_per_cta": warps, "split_symbols": 0}, groups=a.e2e_groups)
+            pipe = R.Pipeline([c], {"warps_per_cta": warps, "split_symbols": 0, "flags": lane_flag},
+                              groups=a.e2e_groups)
             wsb, stb = pipe.sizes
             pws = torch.empty(wsb, dtype=torch.uint8, device=dev)
             stage = torch.empty(stb, dtype=torch.uint8, device=dev)
@@ -552,15 +558,16 @@ def run_adaptive(a):
             "config": {"workload": f"adaptive: 2^27 uint16 latents, symbol i = clip(rint({a.alphabet // 2} + sigma_t Z)) "
                                    f"with t_i ~ clip(rint(N(20, 12)), 0, {a.tables - 1}), {a.tables} log-spaced "
                                    f"Gaussian scale tables (0.11..256) over {a.alphabet} values, n=16, W=32",
-                       "splits": c.info["n_entries"], "warps_per_cta": warps, "autotuned": tuned,
+                       "splits": c.info["n_entries"], "warps_per_cta": warps,
+                       "lanes_per_thread": 2 if lane_flag else 1, "autotuned": tuned,
                        "symbols_bytes": out_bytes,
                        "compressed_bytes": 2 * c.info["n_words"] + 4 * 32, "table_number_bytes": len(s),
                        "l2": "inputs larger than L2 (no flush)", "scale": a.scale},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                         "traffic": (recorded_traffic(f"adaptive w{warps} k{a.splits}")
+                         "traffic": (recorded_traffic(f"adaptive w{warps} k{a.splits} l{2 if lane_flag else 1}")
                                      if a.scale == 1.0 and default_model else None),
-                         "issue": (issue_rate(f"adaptive w{warps} k{a.splits}", mean_ms, dev, clocks)
+                         "issue": (issue_rate(f"adaptive w{warps} k{a.splits} l{2 if lane_flag else 1}", mean_ms, dev, clocks)
                                    if a.scale == 1.0 and default_model else None),
                          "peak_source": peaks["source"],
                          "kernel": "decode_kernel<kAdaptive16>" if a.alphabet <= 256 else "decode_kernel<kAdaptive16Wide>",
@@ -591,14 +598,14 @@ def time_events(fn, cs, steps: int, warmup: int) -> list[float]:
 
 
 def per_stream_round_robin(R, torch, dev, streams, out_ptrs, warps: int, split_symbols: int, n_cuda: int,
-                           steps: int) -> dict:
+                           steps: int, lane_flag: int = 0) -> dict:
     """Per-stream baseline with the batch's own launch shape: one launch per stream (each combined to
     the autotuned split size, the autotuned CTA size), stream i on CUDA stream i mod n_cuda so that
     launches of different streams overlap on the device; one step decodes every stream."""
     main = torch.cuda.current_stream(dev)
     groups = [list(range(g, len(streams), n_cuda)) for g in range(n_cuda)]
     plans = [R.Plan([streams[i] for i in grp], {"warps_per_cta": warps, "split_symbols": split_symbols,
-                                                 "flags": R.BATCH_PER_STREAM}) for grp in groups]
+                                                 "flags": R.BATCH_PER_STREAM | lane_flag}) for grp in groups]
     wss = [torch.empty(max(256, p.workspace_size), dtype=torch.uint8, device=dev) for p in plans]
     side = [torch.cuda.Stream(device=dev) for _ in range(n_cuda)]
     ptrs = [[out_ptrs[i] for i in grp] for grp in groups]
@@ -620,7 +627,8 @@ def per_stream_round_robin(R, torch, dev, streams, out_ptrs, warps: int, split_s
     errors = sum(p.errors(c) for p, c in zip(plans, side))
     assert errors == 0, R.recoil_last_error()
     return {"ms_per_step": statistics.mean(ms), "launches_per_step": sum(p.launches for p in plans),
-            "cuda_streams": n_cuda, "warps_per_cta": warps, "split_symbols": split_symbols}
+            "cuda_streams": n_cuda, "warps_per_cta": warps, "split_symbols": split_symbols,
+            "lanes_per_thread": 2 if lane_flag else 1}
 
 
 def _single_input(R, dist: str, scale: float):
@@ -655,14 +663,15 @@ def configs_block(R, torch, dev, cs, scale: float, steps: int, warmup: int) -> d
     host_s = time.perf_counter() - t0
     res = {"host_encode_s": round(host_s, 1), "scale": scale, "steps": steps, "warmup": warmup}
 
-    def run(streams, out, ref, warps, extra_in=0, tuned=False):
+    def run(streams, out, ref, warps, extra_in=0, tuned=False, lane_flag=0):
         """Decode `streams` into `out` (one tensor; streams concatenated); GB/s, frac, exactness."""
         if tuned and not warps:
             tws = torch.empty(R.autotune_workspace_size(streams), dtype=torch.uint8, device=dev)
             best, _ = R.autotune(streams, [out.data_ptr()], tws, tws.numel(), cs, steps=3, keep_splits=True)
             warps = best["warps_per_cta"]
+            lane_flag = best["flags"] & R.BATCH_TWO_LANES
             del tws
-        plan = R.Plan(streams, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH})
+        plan = R.Plan(streams, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag})
         ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device=dev)
         plan.upload(ws, stream=cs)
         offs, o = [], 0
@@ -677,6 +686,7 @@ def configs_block(R, torch, dev, cs, scale: float, steps: int, warmup: int) -> d
         words = sum(2 * st.info["n_words"] + 4 * 32 for st in streams)
         t = statistics.mean(ms) * 1e-3
         r = {"gbs": round(nbytes / t / 1e9, 1), "us": round(t * 1e6, 1), "warps_per_cta": plan.warps_per_cta,
+             "lanes_per_thread": 2 if lane_flag else 1,
              "splits": sum(st.info["n_entries"] for st in streams),
              "frac": round((nbytes + words + extra_in) / t / 1e9 / peak, 4), "exact": exact}
         del ws
@@ -701,6 +711,7 @@ def configs_block(R, torch, dev, cs, scale: float, steps: int, warmup: int) -> d
         # Recoil against the conventional scheme (Sec. 2.3): the same input cut into 9472 partitions
         # under the same quantised model, each with its own final states; same kernel and CTA size
         warps = z["9472_tuned"]["warps_per_cta"]
+        lf = R.BATCH_TWO_LANES if z["9472_tuned"]["lanes_per_thread"] == 2 else 0
         freq = R.stream_freq(enc)
         parts = np.array_split(s, 9472)
         with ThreadPoolExecutor(max(1, min(64, os.cpu_count() or 1))) as ex:
@@ -708,7 +719,7 @@ def configs_block(R, torch, dev, cs, scale: float, steps: int, warmup: int) -> d
         rec = R.combine_splits(enc, 9472)
         res["recoil_vs_conventional"] = {
             "workload": "1 GiB Zipf(1.2) bytes as one stream at 9472 splits vs 9472 independent partitions",
-            "recoil": run([rec], out, ref, warps), "conventional": run(conv, out, ref, warps),
+            "recoil": run([rec], out, ref, warps, lane_flag=lf), "conventional": run(conv, out, ref, warps, lane_flag=lf),
             "recoil_size_bytes": int(rec.info["bitstream_bytes"] + R.serialized_size(rec)[1]),
             "conventional_size_bytes": int(sum(c.info["bitstream_bytes"] for c in conv) + 8 * len(conv))}
         del conv, parts
@@ -781,8 +792,9 @@ def run_ours(a):
         tws = torch.empty(R.autotune_workspace_size(streams), dtype=torch.uint8, device=dev)
         with torch.cuda.stream(cs):
             best, tms = R.autotune(streams, out_ptrs, tws, tws.numel(), cs, steps=3)
+        lanes = 2 if best["flags"] & R.BATCH_TWO_LANES else 1
         tuned = {"warps_per_cta": best["warps_per_cta"], "split_symbols": best["split_symbols"],
-                 "ms": round(tms, 4)}
+                 "lanes_per_thread": lanes, "ms": round(tms, 4)}
         split_symbols, warps = best["split_symbols"], best["warps_per_cta"]
         del tws
     elif not batch and a.warps == 0:
@@ -790,15 +802,19 @@ def run_ours(a):
         tws = torch.empty(R.autotune_workspace_size(streams), dtype=torch.uint8, device=dev)
         with torch.cuda.stream(cs):
             best, tms = R.autotune(streams, out_ptrs, tws, tws.numel(), cs, steps=3, keep_splits=True)
-        tuned = {"warps_per_cta": best["warps_per_cta"], "split_symbols": 0, "ms": round(tms, 4),
-                 "candidates": "warps per CTA 4, 8, 16 at the workload's split count"}
+        lanes = 2 if best["flags"] & R.BATCH_TWO_LANES else 1
+        tuned = {"warps_per_cta": best["warps_per_cta"], "split_symbols": 0, "lanes_per_thread": lanes,
+                 "ms": round(tms, 4),
+                 "candidates": "one or two lanes a thread x the CTA sizes built for each, at the workload's split count"}
         split_symbols, warps = 0, best["warps_per_cta"]
         del tws
     else:
         split_symbols = (65536 if a.split_symbols < 0 else a.split_symbols) if batch else 0
         warps = a.warps or (8 if batch else 0)         # 0: the library picks the CTA size from the split count
+        lanes = a.lanes or 1
+    lane_flag = R.BATCH_TWO_LANES if lanes == 2 else 0
     opts = {"warps_per_cta": warps, "ctas_per_sm": a.ctas_per_sm, "split_symbols": split_symbols,
-            "flags": R.BATCH_GRAPH}
+            "flags": R.BATCH_GRAPH | lane_flag}
     t_host = time.perf_counter()
     plan = R.Plan(streams, opts)
     plan_ms = (time.perf_counter() - t_host) * 1e3       # host: combining (Sec. 3.3) + descriptors
@@ -870,7 +886,7 @@ def run_ours(a):
             del bws
             if a.rr_streams > 0:
                 rr = per_stream_round_robin(R, torch, dev, streams, out_ptrs, warps, split_symbols or 65536,
-                                            a.rr_streams, a.per_stream_steps)
+                                            a.rr_streams, a.per_stream_steps, lane_flag)
                 exact()
                 rr["value"] = out_bytes / (rr["ms_per_step"] * 1e-3) / 1e9
                 rr["unit"] = "GB/s"
@@ -883,7 +899,7 @@ def run_ours(a):
             sweep = {}
             for k in a.sweep:
                 c = R.combine_splits(encoded[0], k)
-                sp = R.Plan([c], {"warps_per_cta": a.warps, "flags": R.BATCH_GRAPH})
+                sp = R.Plan([c], {"warps_per_cta": a.warps, "flags": R.BATCH_GRAPH | lane_flag})
                 sws = torch.empty(sp.workspace_size, dtype=torch.uint8, device=dev)
                 sp.upload(sws, stream=cs)
                 t = timed(lambda: sp.decode(out_ptrs, cs), 5, 2)
@@ -908,7 +924,7 @@ def run_ours(a):
             # page-locked host memory, decodes and copies the symbols back, every step
             for st in streams:
                 R.stream_pin(st)
-            pipe = R.Pipeline(streams, {k: v for k, v in opts.items() if k != "flags"}, groups=a.e2e_groups)
+            pipe = R.Pipeline(streams, dict(opts, flags=lane_flag), groups=a.e2e_groups)
             wsb, stb = pipe.sizes
             pws = torch.empty(wsb, dtype=torch.uint8, device=dev)
             stage = torch.empty(stb, dtype=torch.uint8, device=dev)
@@ -937,8 +953,8 @@ def run_ours(a):
     value = total_bytes / (mean_ms * 1e-3) / 1e9
     peaks = measured_peaks()
     achieved = (out_bytes + in_bytes) / (mean_ms * 1e-3) / 1e9
-    tkey = (f"batch w{opts['warps_per_cta']} s{split_symbols}" if batch
-            else f"{a.dist} w{opts['warps_per_cta']} k{a.splits}")
+    tkey = (f"batch w{opts['warps_per_cta']} s{split_symbols} l{lanes}" if batch
+            else f"{a.dist} w{opts['warps_per_cta']} k{a.splits} l{lanes}")
     traffic = recorded_traffic(tkey) if a.scale == 1.0 and a.streams == workloads.BATCH_STREAMS else None
     dtype, kernel = kernel_of(plan.streams[0].info)
     line = {
@@ -948,6 +964,7 @@ def run_ours(a):
         "config": {"workload": desc, "symbols_bytes": out_bytes, "compressed_bytes": in_bytes,
                    "splits": sum(st.info["n_entries"] for st in plan.streams) if not batch else None,
                    "split_symbols": split_symbols, "warps_per_cta": opts["warps_per_cta"],
+                   "lanes_per_thread": lanes,
                    "autotuned": tuned,
                    "host_plan_ms": round(plan_ms, 3),
                    "host_combine_us": round(combine_us, 1) if combine_us is not None else None,
