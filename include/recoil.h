@@ -394,7 +394,8 @@ void recoil_pipeline_free(recoil_pipeline* p);
 typedef struct {
   size_t budget_bytes;       /* device memory admitted requests' outputs may use at once (e.g. 20 GiB) */
   uint32_t max_inflight;     /* launches on the device at once, each on its own CUDA stream (default 8) */
-  uint32_t max_batch;        /* requests admitted into one launch (default 64) */
+  uint32_t max_batch;        /* requests admitted into one launch (default 64; up to 4x that when
+                                more than max_batch requests have arrived and wait) */
   uint32_t warps_per_cta;    /* default 8 (4 with RECOIL_SERVE_PER_REQUEST) */
   uint32_t flags;            /* RECOIL_SERVE_* */
   size_t meta_bytes;         /* descriptor area per launch (default 4 MiB) */

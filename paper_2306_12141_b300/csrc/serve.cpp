@@ -5,7 +5,8 @@
 // (a pool stream and an arrival time) are replayed in real time. The loop
 //   - retires finished launches (device events) and frees their memory,
 //   - admits arrived requests in FIFO order while the device-memory budget and
-//     a launch slot allow, up to max_batch per launch,
+//     a launch slot allow, up to max_batch per launch (4 x max_batch when
+//     more than max_batch have arrived and wait),
 //   - combines each admitted stream to its share of the warp slots that are
 //     free at that moment (Sec. 3.3: the decoder's parallelism decides the
 //     split count) by picking entries of the pool stream, whose descriptors
@@ -282,8 +283,29 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
       sl.reqs.clear();
       sl.out_off.clear();
       uint64_t syms_batch = 0;
-      while (next < n_req && req_arrival_s[next] <= t && sl.reqs.size() < max_batch) {
+      // a backlog (more arrived requests than one launch takes) is admitted
+      // up to 4 x max_batch at once: the free warps are shared by more
+      // requests, so each gets fewer splits and the host builds fewer
+      // descriptors per decoded byte; the admission stops before its
+      // descriptors could outgrow the slot's area. Two bounds on its split
+      // count hold: every request's encoded entries, and every free warp plus
+      // each request's long-split minimum, rounding and final entry.
+      const uint32_t free_w0 = total_warps > warps_busy ? total_warps - warps_busy : warps;
+      uint32_t waiting = 0;
+      while (next + waiting < n_req && req_arrival_s[next + waiting] <= t && waiting <= max_batch) waiting++;
+      const size_t cap_n = per_request ? 1 : (waiting > max_batch ? 4 * (size_t)max_batch : max_batch);
+      uint64_t sum_entries = 0, sum_share = free_w0;
+      auto meta_bound = [&](size_t n, uint64_t ents_max) {
+        return sizeof(DevControl) + align_up(n * 8, kAlign) + align_up(n * sizeof(DevStream), kAlign) +
+               align_up(ents_max * sizeof(DevItem), kAlign) + ents_max * sizeof(DevEntry);
+      };
+      while (next < n_req && req_arrival_s[next] <= t && sl.reqs.size() < cap_n) {
         const uint32_t r = next;
+        const Stream& src_r = *pool[req_stream[r]];
+        const uint64_t k_r = src_r.entries.size() + 1;
+        const uint64_t s_r = (src_r.n_syms + max_split - 1) / max_split + warps + 1;
+        const uint64_t bound = per_request ? sum_entries + k_r : std::min(sum_entries + k_r, sum_share + s_r);
+        if (!sl.reqs.empty() && meta_bound(sl.reqs.size() + 1, bound) > meta_cap) break;
         size_t off = 0;
         if (!d_req_outs) {
           if (!heap.alloc(out_bytes[r], &off)) break;        // FIFO: wait for memory
@@ -293,6 +315,8 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
         }
         sl.reqs.push_back(r);
         sl.out_off.push_back(off);
+        sum_entries += k_r;
+        sum_share += s_r;
         syms_batch += pool[req_stream[r]]->n_syms;
         results[r].arrival_s = req_arrival_s[r];
         results[r].admit_s = t;

@@ -116,3 +116,31 @@ def test_admission_bounds_split_length(recoil_lib):
         floor = -(-n // max_split)
         floor = -(-floor // warps) * warps
         assert res["splits"][r] >= min(enc, floor), (r, res["splits"][r], enc, floor)
+
+
+def test_backlog_admits_larger_batches_within_the_descriptor_area(recoil_lib):
+    """Every request arrives at once (a saturating load): admissions take up to 4 x max_batch
+    requests while their descriptors fit the slot's area, with a small area forcing early
+    cuts; every output is the request's input."""
+    R = recoil_lib
+    syms, pool = _pool(R, count=16, seed=57)
+    n_req = 600
+    picks = workloads.request_picks(len(pool), n_req, seed=58)
+    arrive = np.zeros(n_req)
+    outs = [torch.full((max(1, len(syms[p]) * syms[p].itemsize),), 0xAB, dtype=torch.uint8, device="cuda")
+            for p in picks]
+    budget = 1 << 30
+    for meta in (0, 256 << 10):                                   # default 4 MiB, and 256 KiB
+        need = R.serve_arena_size(pool, budget, meta_bytes=meta)
+        arena = torch.empty(need, dtype=torch.uint8, device="cuda")
+        res, stats = R.serve(pool, picks, arrive, arena, need, budget, outs=[o.data_ptr() for o in outs],
+                             max_inflight=4, max_batch=16, meta_bytes=meta, timeout_s=60.0)
+        assert stats["requests"] == n_req
+        per_launch = np.bincount(res["launch"])
+        assert per_launch.max() <= 64
+        if meta == 0:
+            assert per_launch.max() > 16                              # the backlog took larger batches
+        for r, p in enumerate(picks):
+            s = syms[p]
+            assert np.array_equal(outs[r].cpu().numpy()[: len(s) * s.itemsize].view(s.dtype), s), (meta, r)
+            outs[r].fill_(0xAB)
