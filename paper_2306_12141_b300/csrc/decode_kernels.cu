@@ -45,6 +45,8 @@ namespace recoil {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTidBlock = 8 * kW;       // table numbers of one steady block (8 group steps)
+constexpr int kTidSlots = 3;            // staged blocks a warp keeps: current, next, the one after
 
 __device__ __forceinline__ uint32_t lanemask_gt() {
   uint32_t m;
@@ -202,10 +204,21 @@ struct SymOut<kAdaptive16Pair> {
   using T = uint16_t;
 };
 
+__device__ __forceinline__ uint32_t smem_addr32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 // Bring the cache line of p into L1 (no register, no wait).
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" : : "l"(p));
 }
+
+// Asynchronous 8-byte global-to-shared copies (completion tracked per thread
+// in commit groups).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" : : "r"(smem_addr32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" : : : "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" : : "n"(N) : "memory"); }
 
 // A read-only load kept where it is written (volatile asm is neither merged
 // with an earlier load of the same address nor hoisted).
@@ -245,6 +258,8 @@ struct EntryDecoder {
   typename TablesOf<KIND>::T T;
   const uint16_t* __restrict__ words;
   const uint8_t* __restrict__ tid;     // adaptive kinds: PDF row of every symbol index
+  uint8_t* tbuf;                       // adaptive kinds, one lane a thread: kTidSlots staged blocks of table numbers
+  bool staged;                         // the launch stages table numbers in tbuf (else they come through L1)
   uint16_t* ring;
   typename SymOut<KIND>::T* __restrict__ out;
   uint32_t n, mask, gt;
@@ -305,6 +320,18 @@ struct EntryDecoder {
     const int rp0 = w.rp;
     renorm(w, (dec || join) && w.x < kL);
     settle(w, rp0);
+  }
+
+  // Adaptive kinds stage the table numbers of a steady block (groups gtop
+  // down to gtop - 7: 256 bytes, 8 per lane) in shared memory with
+  // asynchronous copies two blocks ahead: the per-symbol read is then a
+  // shared read, not an L1 miss (the L1 holds little next to the tables).
+  // A block that does not exist (below the steady range) copies nothing;
+  // every call commits one group so the waits can count blocks.
+  __device__ __forceinline__ void stage_tids(int gtop, int steady_lo, int slot) {
+    if (gtop - 7 >= steady_lo)
+      cp_async8(tbuf + slot * kTidBlock + lane * 8, tid + (size_t)(gtop - 7) * kW + lane * 8);
+    cp_async_commit();
   }
 
   // A group step where every coder decodes and every symbol is owned (i: its index).
@@ -486,18 +513,59 @@ struct EntryDecoder {
       typename SymOut<KIND>::T* o = out + (size_t)g * kW + lane;
       // 8 steps consume at most 256 words: with p >= cbase at the start of a
       // block, every read stays inside the two staged chunks
-      while (g - 7 >= steady_lo) {
-        const int rp0 = w.rp;
-        const int i0 = g * kW + lane;
-        // adaptive: table numbers of the block after next into L1 (256 bytes, 8 per lane),
-        // only of groups this walk decodes (a shard plan stages no others)
-        if constexpr (is_adaptive<KIND>())
-          if (g - 23 >= steady_lo) prefetch_l1(tid + (g - 23) * kW + lane * 8);
+      if constexpr (is_adaptive<KIND>()) {
+        if (staged) {
+          // the first two blocks' table numbers (only groups this walk
+          // decodes: a shard plan stages no others)
+          stage_tids(g, steady_lo, 0);
+          stage_tids(g - 8, steady_lo, 1);
+          int blk = 0;
+          while (g - 7 >= steady_lo) {
+            const int rp0 = w.rp;
+            // this block's table numbers have landed (the next block's may
+            // not have); then the block after next goes into the slot the
+            // previous block read
+            cp_async_wait<1>();
+            __syncwarp();
+            const uint8_t* tb = tbuf + blk * kTidBlock + lane;
+            stage_tids(g - 16, steady_lo, blk == 0 ? kTidSlots - 1 : blk - 1);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sstep(w, o - u * kW, i0 - u * kW);
-        o -= 8 * kW;
-        g -= 8;
-        settle(w, rp0);
+            for (int u = 0; u < 8; ++u) {
+              const uint32_t s = T.step(w.x, n, mask, tb[(7 - u) * kW]);
+              o[-u * kW] = (typename SymOut<KIND>::T)s;
+              renorm(w, w.x < kL);
+            }
+            blk = blk == kTidSlots - 1 ? 0 : blk + 1;
+            o -= 8 * kW;
+            g -= 8;
+            settle(w, rp0);
+          }
+          cp_async_wait<0>();          // nothing in flight into the buffer once the walk moves on
+          __syncwarp();
+        } else {
+          while (g - 7 >= steady_lo) {
+            const int rp0 = w.rp;
+            const int i0 = g * kW + lane;
+            // table numbers of the block after next into L1 (256 bytes, 8 per lane),
+            // only of groups this walk decodes (a shard plan stages no others)
+            if (g - 23 >= steady_lo) prefetch_l1(tid + (g - 23) * kW + lane * 8);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sstep(w, o - u * kW, i0 - u * kW);
+            o -= 8 * kW;
+            g -= 8;
+            settle(w, rp0);
+          }
+        }
+      } else {
+        while (g - 7 >= steady_lo) {
+          const int rp0 = w.rp;
+          const int i0 = g * kW + lane;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sstep(w, o - u * kW, i0 - u * kW);
+          o -= 8 * kW;
+          g -= 8;
+          settle(w, rp0);
+        }
       }
       for (; g >= steady_lo; --g) {
         const int rp0 = w.rp;
@@ -582,6 +650,8 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS, LANES>::kM
   __shared__ uint32_t s_item;
   const int warp = threadIdx.x >> 5;
   uint16_t* ring = reinterpret_cast<uint16_t*>(smem + a.table_smem) + warp * LANES * kRingSlots;
+  // adaptive kinds, one lane a thread: each warp's staged table numbers follow all rings
+  uint8_t* tbuf = smem + a.table_smem + (size_t)WARPS * LANES * kRingSlots * 2 + (size_t)warp * kTidSlots * kTidBlock;
 
   auto stage = [&](const DevStream& st) {
     const uint4* src = reinterpret_cast<const uint4*>(a.table_pool + st.table);
@@ -596,6 +666,8 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS, LANES>::kM
     d.words = a.word_pool + a.streams[sid].words;
     d.tid = reinterpret_cast<const uint8_t*>(a.word_pool + a.streams[sid].tid);
     d.ring = r;
+    d.tbuf = tbuf;
+    d.staged = LANES == 1 && a.tid_staged;
     d.out = reinterpret_cast<typename SymOut<KIND>::T*>(a.outs[sid]);
     d.n = st.n_bits;
     d.mask = (1u << st.n_bits) - 1u;
@@ -676,8 +748,8 @@ __global__ void __launch_bounds__(WARPS * 32, (Residency<KIND, WARPS, LANES>::kM
   }
 }
 
-size_t smem_bytes(uint32_t warps, uint32_t lanes, uint32_t table_smem) {
-  return (size_t)table_smem + (size_t)warps * lanes * kRingSlots * sizeof(uint16_t);
+size_t smem_bytes(uint32_t kind, uint32_t warps, uint32_t lanes, bool staged, uint32_t table_smem) {
+  return (size_t)table_smem + (size_t)warps * warp_smem(kind, lanes, staged);
 }
 
 // The dynamic shared memory a kernel may use is raised only when a launch
@@ -703,7 +775,7 @@ cudaError_t allow_smem(size_t sm, bool force) {
 
 template <uint32_t KIND, int WARPS, int LANES>
 cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  const size_t sm = smem_bytes(WARPS, LANES, a.table_smem);
+  const size_t sm = smem_bytes(KIND, WARPS, LANES, a.tid_staged != 0, a.table_smem);
   for (int attempt = 0; attempt < 2; attempt++) {
     cudaError_t e = allow_smem<KIND, WARPS, LANES>(sm, attempt > 0);
     if (e != cudaSuccess) return e;
@@ -715,8 +787,8 @@ cudaError_t launch_kw(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
 }
 
 template <uint32_t KIND, int WARPS, int LANES>
-int occupancy_kw(uint32_t table_smem, int* out) {
-  const size_t sm = smem_bytes(WARPS, LANES, table_smem);
+int occupancy_kw(uint32_t table_smem, bool staged, int* out) {
+  const size_t sm = smem_bytes(KIND, WARPS, LANES, staged, table_smem);
   if (allow_smem<KIND, WARPS, LANES>(sm, false) != cudaSuccess) return -1;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, decode_kernel<KIND, WARPS, LANES>, WARPS * 32, sm) ==
                  cudaSuccess
@@ -774,10 +846,10 @@ cudaError_t launch_k(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
 }
 
 template <uint32_t KIND>
-int occupancy_k(uint32_t warps, uint32_t lanes, uint32_t table_smem, int* out) {
+int occupancy_k(uint32_t warps, uint32_t lanes, bool staged, uint32_t table_smem, int* out) {
   return by_shape<KIND>(warps, lanes, [&](auto w, auto l) -> int {
     if constexpr (decltype(w)::value == 0) return -1;
-    else return occupancy_kw<KIND, decltype(w)::value, decltype(l)::value>(table_smem, out);
+    else return occupancy_kw<KIND, decltype(w)::value, decltype(l)::value>(table_smem, staged, out);
   });
 }
 
@@ -807,20 +879,23 @@ cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cud
   return cudaErrorInvalidValue;
 }
 
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t lanes, uint32_t table_smem, int* out) {
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t lanes, bool staged, uint32_t table_smem, int* out) {
   switch (kind) {
-    case kPacked8: return occupancy_k<kPacked8>(warps, lanes, table_smem, out);
-    case kGeneric8: return occupancy_k<kGeneric8>(warps, lanes, table_smem, out);
-    case kGeneric16: return occupancy_k<kGeneric16>(warps, lanes, table_smem, out);
-    case kAdaptive8: return occupancy_k<kAdaptive8>(warps, lanes, table_smem, out);
-    case kAdaptive16: return occupancy_k<kAdaptive16>(warps, lanes, table_smem, out);
-    case kAdaptive16Wide: return occupancy_k<kAdaptive16Wide>(warps, lanes, table_smem, out);
-    case kAdaptive8Pair: return occupancy_k<kAdaptive8Pair>(warps, lanes, table_smem, out);
-    case kAdaptive16Pair: return occupancy_k<kAdaptive16Pair>(warps, lanes, table_smem, out);
+    case kPacked8: return occupancy_k<kPacked8>(warps, lanes, staged, table_smem, out);
+    case kGeneric8: return occupancy_k<kGeneric8>(warps, lanes, staged, table_smem, out);
+    case kGeneric16: return occupancy_k<kGeneric16>(warps, lanes, staged, table_smem, out);
+    case kAdaptive8: return occupancy_k<kAdaptive8>(warps, lanes, staged, table_smem, out);
+    case kAdaptive16: return occupancy_k<kAdaptive16>(warps, lanes, staged, table_smem, out);
+    case kAdaptive16Wide: return occupancy_k<kAdaptive16Wide>(warps, lanes, staged, table_smem, out);
+    case kAdaptive8Pair: return occupancy_k<kAdaptive8Pair>(warps, lanes, staged, table_smem, out);
+    case kAdaptive16Pair: return occupancy_k<kAdaptive16Pair>(warps, lanes, staged, table_smem, out);
   }
   return -1;
 }
 
-size_t ring_smem_per_warp() { return (size_t)kRingSlots * sizeof(uint16_t); }
+size_t warp_smem(uint32_t kind, uint32_t lanes, bool staged) {
+  const size_t l = lanes > 1 ? lanes : 1;
+  return l * kRingSlots * sizeof(uint16_t) + (is_adaptive_kind(kind) && l == 1 && staged ? (size_t)kTidSlots * kTidBlock : 0);
+}
 
 }  // namespace recoil

@@ -147,6 +147,7 @@ struct LaunchArgs {
   uint32_t warps;            // warps per CTA
   uint32_t warp_queue;       // 1: every item is one entry and all share one table; warps pop items alone
   uint32_t lanes;            // coder lanes a thread (splits a warp decodes at once): 1 (0 reads as 1) or 2
+  uint32_t tid_staged;       // adaptive kinds, one lane a thread: stage table numbers in shared memory
 };
 
 // Grid of a persistent launch: enough CTAs for the items, at most the resident ones.
@@ -159,8 +160,11 @@ inline unsigned launch_grid(const LaunchArgs& a, int ctas_per_sm, int sms) {
 
 // Kernel launchers (decode_kernels.cu).
 cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cudaStream_t s);
-int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t lanes, uint32_t table_smem, int* out);
-size_t ring_smem_per_warp();   // one split's word ring; a warp holds one per lane a thread
+int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t lanes, bool staged, uint32_t table_smem, int* out);
+// Shared memory a warp of a `kind` kernel holds besides the tables: a word ring
+// per lane a thread, and for adaptive kinds at one lane a thread whose launch
+// stages them the table numbers of three steady blocks.
+size_t warp_smem(uint32_t kind, uint32_t lanes, bool staged);
 bool warps_supported(uint32_t warps);   // CTA sizes the kernels are built for: 1, 2, 4, 8, 16, 32 warps
 bool adaptive_warps_supported(uint32_t warps);   // adaptive kinds: 4, 8, 16, 32 warps
 // CTA shapes built: one lane a thread as above; two lanes a thread: static

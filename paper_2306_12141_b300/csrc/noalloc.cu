@@ -96,7 +96,7 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
   for (uint32_t k = 0; k < kKinds; k++) {
     if (!img.kind_count[k]) continue;
     const uint32_t smem = (uint32_t)((img.kind_smem[k] + 15) / 16 * 16);
-    if (occupancy_ctas_per_sm(k, img.warps, img.lanes, smem, &per_sm[k]) != 0 || per_sm[k] <= 0) {
+    if (occupancy_ctas_per_sm(k, img.warps, img.lanes, img.kind_staged[k] != 0, smem, &per_sm[k]) != 0 || per_sm[k] <= 0) {
       recoil_plan_free(plan);
       return fail(RECOIL_ECUDA, "occupancy query failed");
     }
@@ -130,6 +130,7 @@ extern "C" int recoil_decode_noalloc(const recoil_stream* s, const void* d_words
     a.persistent = 1;
     a.table_smem = (uint32_t)((img.kind_smem[k] + 15) / 16 * 16);
     a.warp_queue = img.kind_warp_queue[k];
+    a.tid_staged = img.kind_staged[k];
     e = launch_decode(k, a, launch_grid(a, per_sm[k], sms), cs);
   }
   // read the error flags back (this also makes the call return after the decode)

@@ -254,6 +254,7 @@ struct recoil_plan {
   std::vector<uint64_t> tid_lo, tid_cnt;               // per adaptive stream: first staged symbol and how many
   uint32_t n_items = 0;
   uint32_t kind_first[kKinds] = {}, kind_count[kKinds] = {}, kind_smem[kKinds] = {}, kind_warp_queue[kKinds] = {};
+  uint32_t kind_staged[kKinds] = {};                   // adaptive launch kinds staging table numbers in shared memory
   std::vector<uint32_t> stream_kind, stream_item_first, stream_item_count;
   // shard plans (one stream): only entries [entry_first, entry_last) get work
   // items; the others stay in the entry array as the previous-entry guards
@@ -327,7 +328,9 @@ static void choose_guides(const recoil_plan* P, uint32_t* guide) {
     paired[k] = std::max(paired[k], bytes);
     pairable[k] = pairable[k] && bytes > 0;
   }
-  const size_t rings = (size_t)P->warps * P->lanes * ring_smem_per_warp() + 16;
+  // every adaptive kind alike; table-number staging is decided afterwards,
+  // only where it costs neither guide width nor residency
+  const size_t rings = (size_t)P->warps * warp_smem(kAdaptive8, P->lanes, false) + 16;
   const uint64_t per_cta = (uint64_t)P->warps * P->lanes;   // splits a CTA decodes at once
   const uint64_t sms = (uint64_t)device_sms();
   for (uint32_t k = 0; k < kKinds; k++) {
@@ -500,8 +503,20 @@ static int plan_build(recoil_plan* P) {
     }
   }
   for (uint32_t k = 0; k < kKinds; k++) {
-    if (P->kind_smem[k] + warps * P->lanes * ring_smem_per_warp() > kMaxSmem)
+    if (P->kind_smem[k] + warps * warp_smem(k, P->lanes, false) > kMaxSmem)
       return fail(RECOIL_EINVAL, "decoder tables too large for shared memory (alphabet or n too large)");
+    // adaptive kinds at one lane a thread stage each steady block's table
+    // numbers in shared memory where that still fits and keeps as many CTAs
+    // resident; the L1 holds little next to their tables. Measured: paired
+    // latents +4%, wide alphabets +9%; the one-byte-guide kinds over up to
+    // 256 symbols -1 to -2%, so those keep the L1 path
+    P->kind_staged[k] = 0;
+    if (is_adaptive_kind(k) && k != kAdaptive8 && k != kAdaptive16 && P->lanes == 1 && P->kind_smem[k]) {
+      const size_t plain = P->kind_smem[k] + warps * warp_smem(k, 1, false) + 16;
+      const size_t staged = P->kind_smem[k] + warps * warp_smem(k, 1, true) + 16;
+      if (staged <= kMaxSmem && adaptive_ctas_per_sm(warps, 1, staged) >= adaptive_ctas_per_sm(warps, 1, plain))
+        P->kind_staged[k] = 1;
+    }
   }
   // Kinds whose items all decode with one table (one stream, or streams with
   // identical models) are staged once per CTA; their entries become items of
@@ -594,6 +609,7 @@ void plan_image(const recoil_plan* P, PlanImage* o) {
     o->kind_count[k] = P->kind_count[k];
     o->kind_smem[k] = P->kind_smem[k];
     o->kind_warp_queue[k] = P->kind_warp_queue[k];
+    o->kind_staged[k] = P->kind_staged[k];
   }
 }
 }  // namespace recoil
@@ -734,8 +750,9 @@ static int plan_launch(recoil_plan* P, cudaStream_t cs) {
     a.persistent = 1;
     a.table_smem = (uint32_t)align_up(P->kind_smem[k], 16);
     a.warp_queue = P->kind_warp_queue[k];
+    a.tid_staged = P->kind_staged[k];
     int per_sm = (int)P->opts.ctas_per_sm;
-    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, P->lanes, a.table_smem, &per_sm) != 0)
+    if (per_sm <= 0 && occupancy_ctas_per_sm(k, P->warps, P->lanes, a.tid_staged != 0, a.table_smem, &per_sm) != 0)
       return fail(RECOIL_ECUDA, "occupancy query failed");
     if (per_sm <= 0) return fail(RECOIL_EINVAL, "kernel does not fit on an SM with these options");
     const unsigned grid = launch_grid(a, per_sm, P->sms);

@@ -69,6 +69,7 @@ struct PlanImage {
   uint32_t warps;
   uint32_t lanes;            // coder lanes a thread
   uint32_t kind_first[kKinds], kind_count[kKinds], kind_smem[kKinds], kind_warp_queue[kKinds];
+  uint32_t kind_staged[kKinds];   // adaptive launch kinds that stage table numbers in shared memory
 };
 }  // namespace recoil
 struct recoil_plan;

@@ -164,7 +164,8 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   if (e != cudaSuccess) return fail(RECOIL_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
   int per_sm[kKinds] = {};
   for (uint32_t k = 0; k < kKinds; k++)
-    if (occupancy_ctas_per_sm(k, warps, 1, kind_smem[k], &per_sm[k]) != 0 || per_sm[k] <= 0) per_sm[k] = 1;
+    if (occupancy_ctas_per_sm(k, warps, 1, img.kind_staged[k] != 0, kind_smem[k], &per_sm[k]) != 0 || per_sm[k] <= 0)
+      per_sm[k] = 1;
   const uint32_t total_warps = (uint32_t)(per_sm[kPacked8] * sms) * warps;
 
   std::vector<Slot> slots(nslots);
@@ -423,6 +424,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
           a.kind = k;
           a.persistent = 1;
           a.table_smem = kind_smem[k];
+          a.tid_staged = img.kind_staged[k];
           const unsigned grid = (unsigned)std::min<uint64_t>(a.n_items, (uint64_t)per_sm[k] * sms);
           e = launch_decode(k, a, grid, sl.stream);
           warps_launch += grid * warps;
