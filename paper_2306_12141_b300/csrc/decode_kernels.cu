@@ -135,7 +135,10 @@ struct AdaptiveTables {
 // symbol s the u32 H(s) | H(s+1) << 16, with H as above, and guide entry b of
 // row t the u16 lo | hi << 8 of the symbols owning the first slots of buckets
 // b and b + 1 (2^9 buckets): one read brackets the symbol, one read of the
-// row gives F(s) and f(s) once the bracket is closed.
+// row gives F(s) and f(s) once the bracket is closed. A bracket of two
+// symbols (the usual case when it is not closed) is decided by H(s+1), the
+// high half of row[s], with row[s+1] read beside it: no search loop, no
+// third dependent read; wider brackets fall back to bisection.
 struct PairTables {
   const uint32_t* pairs;
   const uint16_t* guide;
@@ -152,13 +155,27 @@ struct PairTables {
     const uint32_t* row = pairs + t * stride;
     const uint32_t g = guide[t * gstride + (slot >> gshift)];
     uint32_t s = g & 0xffu;
-    uint32_t hi = g >> 8;
     const uint16_t* low = reinterpret_cast<const uint16_t*>(row);   // H(s) at low[2 s] (little-endian)
-    while (s < hi) {                                    // bounded: hi - s halves
-      const uint32_t mid = (s + hi + 1) >> 1;
-      if (low[2 * mid] < slot) s = mid; else hi = mid - 1;
+    const uint32_t hi = g >> 8;
+    uint32_t p = row[s];
+    if (s < hi) {
+      // more than one symbol in the bracket: H(s+1), the high half of p,
+      // decides between s and s + 1, with row[s+1] read beside row[s]
+      const uint32_t p1 = row[s + 1];
+      if ((p >> 16) < slot) {
+        s += 1;
+        p = p1;
+        if (s < hi && (p >> 16) < slot) {               // three or more: bisect the rest
+          uint32_t a = s + 1, b = hi;
+          while (a < b) {                               // bounded: b - a halves
+            const uint32_t mid = (a + b + 1) >> 1;
+            if (low[2 * mid] < slot) a = mid; else b = mid - 1;
+          }
+          s = a;
+          p = row[s];
+        }
+      }
     }
-    const uint32_t p = row[s];
     const uint32_t h0 = p & 0xffffu;
     const uint32_t f = ((p >> 16) - h0) & 0xffffu;
     x = f * (x >> n) + slot - ((h0 + 1u) & 0xffffu);
