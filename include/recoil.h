@@ -394,11 +394,11 @@ void recoil_pipeline_free(recoil_pipeline* p);
 typedef struct {
   size_t budget_bytes;       /* device memory admitted requests' outputs may use at once (e.g. 20 GiB) */
   uint32_t max_inflight;     /* launches on the device at once, each on its own CUDA stream (default 8) */
-  uint32_t max_batch;        /* requests admitted into one launch (default 64; up to 4x that when
+  uint32_t max_batch;        /* requests admitted into one launch (default 64; up to 8x that when
                                 more than max_batch requests have arrived and wait) */
   uint32_t warps_per_cta;    /* default 8 (4 with RECOIL_SERVE_PER_REQUEST) */
   uint32_t flags;            /* RECOIL_SERVE_* */
-  size_t meta_bytes;         /* descriptor area per launch (default 4 MiB) */
+  size_t meta_bytes;         /* descriptor area per launch (default 16 MiB) */
   double timeout_s;          /* wall-clock limit of the run (default 60 s) */
   uint32_t max_split_symbols; /* longest split a request is combined to (default 131072): a
                                  split is one warp's sequential work, so this bounds latency */

@@ -119,7 +119,7 @@ def test_admission_bounds_split_length(recoil_lib):
 
 
 def test_backlog_admits_larger_batches_within_the_descriptor_area(recoil_lib):
-    """Every request arrives at once (a saturating load): admissions take up to 4 x max_batch
+    """Every request arrives at once (a saturating load): admissions take up to 8 x max_batch
     requests while their descriptors fit the slot's area, with a small area forcing early
     cuts; every output is the request's input."""
     R = recoil_lib
@@ -130,14 +130,14 @@ def test_backlog_admits_larger_batches_within_the_descriptor_area(recoil_lib):
     outs = [torch.full((max(1, len(syms[p]) * syms[p].itemsize),), 0xAB, dtype=torch.uint8, device="cuda")
             for p in picks]
     budget = 1 << 30
-    for meta in (0, 256 << 10):                                   # default 4 MiB, and 256 KiB
+    for meta in (0, 256 << 10):                                   # default 16 MiB, and 256 KiB
         need = R.serve_arena_size(pool, budget, meta_bytes=meta)
         arena = torch.empty(need, dtype=torch.uint8, device="cuda")
         res, stats = R.serve(pool, picks, arrive, arena, need, budget, outs=[o.data_ptr() for o in outs],
                              max_inflight=4, max_batch=16, meta_bytes=meta, timeout_s=60.0)
         assert stats["requests"] == n_req
         per_launch = np.bincount(res["launch"])
-        assert per_launch.max() <= 64
+        assert per_launch.max() <= 128
         if meta == 0:
             assert per_launch.max() > 16                              # the backlog took larger batches
         for r, p in enumerate(picks):
