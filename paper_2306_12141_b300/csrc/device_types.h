@@ -59,11 +59,11 @@ __host__ __device__ constexpr uint32_t adaptive_guide_entry_bytes(uint32_t k) { 
 // The guide of a row: 2^g buckets over the 2^n slots (at most 2^n). A plan
 // stages g = 9, or 10 where it can afford twice the guide's shared memory,
 // or 0 (one bucket: the whole row is searched) where even 9 does not fit, or
-// the paired layout with 2^9 buckets (kGuidePairs, for one-byte entries).
+// the paired layout with 2^10 buckets (kGuidePairs, for one-byte entries).
 constexpr uint32_t kGuideBits = 9;
 constexpr uint32_t kGuideBitsFine = 10;
 constexpr uint32_t kGuideBitsNone = 0;
-constexpr uint32_t kGuidePairs = 0x100 | kGuideBits;   // variant code, not a width: 2^9 buckets, paired
+constexpr uint32_t kGuidePairs = 0x100 | kGuideBitsFine;   // variant code, not a width: 2^10 buckets, paired
 
 // Longest alphabet of an adaptive model (the decoder's CDF search covers 2^12 symbols).
 constexpr uint32_t kMaxAdaptiveAlphabet = 4096;
@@ -101,9 +101,10 @@ struct alignas(16) DevStream {
     uint32_t guide_bits;     // adaptive kinds: log2 of the guide buckets per row
   };
   uint32_t row_stride;       // adaptive: entries between CDF rows, an odd number of 32-bit words
-                             // (16-bit entries; paired kinds: 32-bit entries)
+                             // (16-bit entries; paired kinds: 32-bit words between a PDF's blocks)
   uint32_t n_tables;         // adaptive: CDF rows
-  uint32_t guide_stride;     // adaptive kinds: bytes between guide rows (after all CDF rows; one entry per bucket boundary)
+  uint32_t guide_stride;     // adaptive kinds: bytes between guide rows (after all CDF rows; one entry per bucket
+                             // boundary); paired kinds: byte offset of the guide within a PDF's block
 };
 static_assert(sizeof(DevStream) == 64, "DevStream layout");
 

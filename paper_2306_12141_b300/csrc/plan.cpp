@@ -50,19 +50,21 @@ uint32_t guide_stride(uint32_t n, uint32_t g, uint32_t eb) {
   return 4 * words;
 }
 
-// Paired layout (one-byte guide entries only): u32 entries between CDF rows
-// (one per symbol, H(s) | H(s+1) << 16), an odd number so that rows start in
-// different banks, and bytes between guide rows (2^g u16 entries, g = 9 or n).
-uint32_t pair_row_stride(uint32_t A) { return A | 1u; }
-uint32_t pair_guide_stride(uint32_t n) {
-  uint32_t words = ((1u << guide_bits(n, kGuideBits)) * 2 + 3) / 4;
+// Paired layout (one-byte guide entries only): a block per PDF, an odd
+// number of 32-bit words apart so that blocks start in different banks: the
+// u32 F(s) | H(s+1) << 16 of each symbol (F(s) modulo 2^16: exact for every
+// symbol of nonzero frequency), then the guide row, one byte for each of the
+// 2^g + 1 bucket boundaries (g = 10, or n if smaller).
+uint32_t pair_guide_bits(uint32_t n) { return guide_bits(n, kGuideBitsFine); }
+uint32_t pair_block_words(uint32_t A, uint32_t n) {
+  uint32_t words = A + ((1u << pair_guide_bits(n)) + 1 + 3) / 4;
   if (!(words & 1)) words++;
-  return 4 * words;
+  return words;
 }
 
 // An adaptive stream's table image holds four variants: the CDF rows followed
 // by a guide row per PDF with 2^9 buckets, with 2^10 buckets, with one bucket,
-// and (one-byte guide entries only) the paired layout with 2^9 buckets; a
+// and (one-byte guide entries only) the paired layout with 2^10 buckets; a
 // plan stages one of them. The variants in image order:
 constexpr uint32_t kGuideVariants[4] = {kGuideBits, kGuideBitsFine, kGuideBitsNone, kGuidePairs};
 
@@ -71,7 +73,7 @@ size_t variant_bytes(const Stream& s, uint32_t v) {
   const uint32_t eb = adaptive_guide_entry_bytes(table_kind_of(s));
   if (v == kGuidePairs) {
     if (eb != 1) return 0;
-    return align_up((size_t)s.n_tables * ((size_t)pair_row_stride(s.alphabet()) * 4 + pair_guide_stride(s.n_bits)), 16);
+    return align_up((size_t)s.n_tables * pair_block_words(s.alphabet(), s.n_bits) * 4, 16);
   }
   const size_t rows = (size_t)s.n_tables * adaptive_row_stride(s.alphabet()) * 2;
   return align_up(rows + (size_t)s.n_tables * guide_stride(s.n_bits, v, eb), 16);
@@ -137,27 +139,25 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
         }
       }
       if (eb == 1) {
-        // paired layout: u32 H(s) | H(s+1) << 16 per symbol, then per bucket the
-        // u16 owner(first slot of b) | owner(first slot of b + 1) << 8
+        // paired layout: per PDF, u32 F(s) | H(s+1) << 16 per symbol, then per
+        // bucket boundary b the symbol owning slot b << (n - g) (the last slot
+        // for b = 2^g)
         guide_variant(s, kGuidePairs, &off, &bytes);
-        const uint32_t pstride = pair_row_stride(A), gb = guide_bits(n, kGuideBits);
-        uint32_t* prow = reinterpret_cast<uint32_t*>(s.table_img.data() + off);
-        uint16_t* pguide = reinterpret_cast<uint16_t*>(s.table_img.data() + off + (size_t)s.n_tables * pstride * 4);
-        const uint32_t gstride = pair_guide_stride(n) / 2;
-        std::vector<uint32_t> owner((1u << gb) + 1);
+        const uint32_t bw = pair_block_words(A, n), gb = pair_guide_bits(n);
         for (uint32_t t = 0; t < s.n_tables; t++) {
+          uint8_t* blk = s.table_img.data() + off + (size_t)t * bw * 4;
           F[0] = 0;
           for (uint32_t sym = 0; sym < A; sym++) F[sym + 1] = F[sym] + s.freq[(size_t)t * A + sym];
-          for (uint32_t sym = 0; sym < A; sym++)
-            prow[(size_t)t * pstride + sym] = ((F[sym] - 1) & 0xffffu) | (((F[sym + 1] - 1) & 0xffffu) << 16);
+          for (uint32_t sym = 0; sym < A; sym++) {
+            const uint32_t v = (F[sym] & 0xffffu) | (((F[sym + 1] - 1) & 0xffffu) << 16);
+            std::memcpy(blk + (size_t)sym * 4, &v, 4);
+          }
           uint32_t sym = 0;
           for (uint32_t b = 0; b <= (1u << gb); b++) {
             const uint32_t slot = std::min<uint32_t>(b << (n - gb), (1u << n) - 1);
             while (F[sym + 1] <= slot) sym++;
-            owner[b] = sym;
+            blk[(size_t)A * 4 + b] = (uint8_t)sym;
           }
-          for (uint32_t b = 0; b < (1u << gb); b++)
-            pguide[(size_t)t * gstride + b] = (uint16_t)(owner[b] | (owner[b + 1] << 8));
         }
       }
     } else if (k == kPacked8) {
@@ -453,9 +453,9 @@ static int plan_build(recoil_plan* P) {
         d.table += voff;
         d.table_bytes = (uint32_t)vbytes;
         if (g == kGuidePairs) {
-          d.row_stride = pair_row_stride(s.alphabet());
-          d.guide_bits = guide_bits(s.n_bits, kGuideBits);
-          d.guide_stride = pair_guide_stride(s.n_bits);
+          d.row_stride = pair_block_words(s.alphabet(), s.n_bits);
+          d.guide_bits = pair_guide_bits(s.n_bits);
+          d.guide_stride = s.alphabet() * 4;
         } else {
           d.row_stride = adaptive_row_stride(s.alphabet());
           d.guide_bits = guide_bits(s.n_bits, g);
