@@ -285,6 +285,26 @@ struct EntryDecoder {
       return T.step(x, n, mask);
   }
 
+  // Eq. 2 for symbol i with its table number from the staged buffer at byte
+  // toff (toff >= 0), else read like dec does
+  __device__ __forceinline__ uint32_t dec_at(uint32_t& x, int i, int toff) const {
+    if constexpr (is_adaptive<KIND>())
+      return T.step(x, n, mask, toff >= 0 ? (uint32_t)tbuf[toff] : (uint32_t)__ldg(tid + i));
+    else
+      return T.step(x, n, mask);
+  }
+
+  // Where this lane's table number of group gg sits in the staged buffer when
+  // it holds the kTidSlots blocks of 8 groups from group go down, the first in
+  // slot b0 and the next ones in the slots after it (wrapping); -1 if outside.
+  __device__ __forceinline__ int toff_of(int go, int b0, int gg) const {
+    const int off = go - gg;
+    if (off < 0 || off >= kTidSlots * 8) return -1;
+    int slot = b0 + (off >> 3);
+    if (slot >= kTidSlots) slot -= kTidSlots;
+    return slot * kTidBlock + (7 - (off & 7)) * kW + lane;
+  }
+
   __device__ __forceinline__ void refill(Walker& w) {
     __syncwarp();
     const int cnew = (w.cbase >> 8) - 2;
@@ -319,12 +339,12 @@ struct EntryDecoder {
   // previous split's metadata is exactly the state this thread carries across
   // the boundary (Sec. 3.1, 4.1.3), so any corrupt word or state shows here.
   __device__ __forceinline__ void pstep(Walker& w, int g, int act, uint32_t x0, int lo, int hi1,
-                                        int act_p, uint32_t x_p, bool& bad) {
+                                        int act_p, uint32_t x_p, bool& bad, int toff = -1) {
     const int i = g * kW + lane;
     const bool dec = (g < act) && (i >= lo);
     const bool join = (g == act);
     if (dec) {
-      const uint32_t s = this->dec(w.x, i);
+      const uint32_t s = this->dec_at(w.x, i, toff);
       if (i < hi1) out[i] = (typename SymOut<KIND>::T)s;
     }
     if (join) w.x = x0;
@@ -334,14 +354,15 @@ struct EntryDecoder {
     settle(w, rp0);
   }
 
-  // Adaptive kinds stage the table numbers of a steady block (groups gtop
-  // down to gtop - 7: 256 bytes, 8 per lane) in shared memory with
-  // asynchronous copies two blocks ahead: the per-symbol read is then a
-  // shared read, not an L1 miss (the L1 holds little next to the tables).
-  // A block that does not exist (below the steady range) copies nothing;
-  // every call commits one group so the waits can count blocks.
-  __device__ __forceinline__ void stage_tids(int gtop, int steady_lo, int slot) {
-    if (gtop - 7 >= steady_lo)
+  // Adaptive kinds stage table numbers in shared memory with asynchronous
+  // copies, in blocks of 8 groups (256 bytes, 8 per lane): the per-symbol
+  // read is then a shared read, not an L1 miss (the L1 holds little next to
+  // the tables). The steady loop stages two blocks ahead; the synchronisation
+  // phase at the top and the groups below the steady loop read blocks staged
+  // beforehand. Chunks of groups below glo (the walk's lowest group) are not
+  // copied; every call commits one group so the waits can count blocks.
+  __device__ __forceinline__ void stage_tids(int gtop, int glo, int slot) {
+    if (gtop - 7 + (lane >> 2) >= glo)
       cp_async8(tbuf + slot * kTidBlock + lane * 8, tid + (size_t)(gtop - 7) * kW + lane * 8);
     cp_async_commit();
   }
@@ -503,6 +524,11 @@ struct EntryDecoder {
       if (c >= 1) put_chunk(ring, c - 1, lane, b);
       w.pre = load_chunk(words, c - 2, lane);
     }
+    // table numbers of the synchronisation phase: the three blocks from the
+    // top group, copied while the ring's chunks load
+    const bool st = is_adaptive<KIND>() ? staged : false;
+    if (st)
+      for (int k = 0; k < kTidSlots; ++k) stage_tids(g - 8 * k, lo >> 5, k);
     __syncwarp();
     w.rp = (w.p & (kRingWords - 1)) + kRingWords;
 
@@ -519,7 +545,13 @@ struct EntryDecoder {
     const int steady_lo = max((lo + kW - 1) >> 5, gtop_p + 1);   // ... fully decodable, above the check
     bool bad = false;
 
-    for (; g > steady_hi && g >= (lo >> 5); --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
+    int go = g, b0 = 0;                     // staged blocks: from group go down, the first in slot b0
+    if (st) {
+      cp_async_wait<0>();
+      __syncwarp();
+    }
+    for (; g > steady_hi && g >= (lo >> 5); --g)
+      pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad, st ? toff_of(go, b0, g) : -1);
 
     if (g >= steady_lo) {
       typename SymOut<KIND>::T* o = out + (size_t)g * kW + lane;
@@ -528,9 +560,11 @@ struct EntryDecoder {
       if constexpr (is_adaptive<KIND>()) {
         if (staged) {
           // the first two blocks' table numbers (only groups this walk
-          // decodes: a shard plan stages no others)
-          stage_tids(g, steady_lo, 0);
-          stage_tids(g - 8, steady_lo, 1);
+          // decodes: a shard plan stages no others), once every lane has
+          // read the synchronisation phase's
+          __syncwarp();
+          stage_tids(g, lo >> 5, 0);
+          stage_tids(g - 8, lo >> 5, 1);
           int blk = 0;
           while (g - 7 >= steady_lo) {
             const int rp0 = w.rp;
@@ -540,7 +574,7 @@ struct EntryDecoder {
             cp_async_wait<1>();
             __syncwarp();
             const uint8_t* tb = tbuf + blk * kTidBlock + lane;
-            stage_tids(g - 16, steady_lo, blk == 0 ? kTidSlots - 1 : blk - 1);
+            stage_tids(g - 16, lo >> 5, blk == 0 ? kTidSlots - 1 : blk - 1);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const uint32_t s = T.step(w.x, n, mask, tb[(7 - u) * kW]);
@@ -552,8 +586,13 @@ struct EntryDecoder {
             g -= 8;
             settle(w, rp0);
           }
-          cp_async_wait<0>();          // nothing in flight into the buffer once the walk moves on
+          // the block after next as well: the groups below the steady loop
+          // read the three blocks from here; nothing stays in flight
+          stage_tids(g - 16, lo >> 5, blk == 0 ? kTidSlots - 1 : blk - 1);
+          cp_async_wait<0>();
           __syncwarp();
+          go = g;
+          b0 = blk;
         } else {
           while (g - 7 >= steady_lo) {
             const int rp0 = w.rp;
@@ -581,7 +620,8 @@ struct EntryDecoder {
       }
       for (; g >= steady_lo; --g) {
         const int rp0 = w.rp;
-        sstep(w, o, g * kW + lane);
+        *o = (typename SymOut<KIND>::T)dec_at(w.x, g * kW + lane, st ? toff_of(go, b0, g) : -1);
+        renorm(w, w.x < kL);
         o -= kW;
         settle(w, rp0);
       }
@@ -597,7 +637,7 @@ struct EntryDecoder {
       act_p = ld_keep(&ent[-1].act[lane]);
       x_p = (uint32_t)ld_keep(reinterpret_cast<const int*>(&ent[-1].x0[lane]));
     }
-    for (; g >= (lo >> 5); --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad);
+    for (; g >= (lo >> 5); --g) pstep(w, g, act, x0, lo, hi1, act_p, x_p, bad, st ? toff_of(go, b0, g) : -1);
 
     // The first thread of a stream must end where the encoder started (Eqs. 1-4 invert).
     uint32_t err = 0;
