@@ -158,9 +158,9 @@ def test_gpu_adaptive_matches_oracle(recoil_lib, cfg):
                          ids=lambda c: f"n{c['n_bits']}_A{c['alphabet']}_T{c['n_tables']}")
 @pytest.mark.parametrize("warps", [8, 32])
 def test_gpu_adaptive_paired_and_byte_layouts(recoil_lib, cfg, warps):
-    """Alphabets up to 256 have two staged layouts: the paired one (u32 H(s) | H(s+1) << 16
-    per symbol, a u16 bracket per guide bucket) where it keeps as many splits resident, and
-    the one-byte guide layout (RECOIL_BATCH_NO_PAIRS forces it). Both decode to the input
+    """Alphabets up to 256 have two staged layouts: the paired one (a block per PDF: u32
+    F(s) | H(s+1) << 16 per symbol, then a byte per boundary of 2^10 guide buckets) where it
+    keeps as many splits resident, and the one-byte guide layout (RECOIL_BATCH_NO_PAIRS forces it). Both decode to the input
     and to the oracle's split decode; the paired image is the larger one when it is staged."""
     R = recoil_lib
     a, tables, s, tid = _case(300_007, 26, **cfg)
@@ -183,7 +183,7 @@ def test_gpu_adaptive_paired_and_byte_layouts(recoil_lib, cfg, warps):
 
 
 def test_adaptive_paired_layout_staged_where_it_fits(recoil_lib):
-    """Host side of the layout choice: 64 PDFs over 256 symbols at n = 16 take 132 KB paired,
+    """Host side of the layout choice: 64 PDFs over 256 symbols at n = 16 take 131 KB paired,
     which fits beside the rings of one 32-warp CTA (as the 2^10-bucket byte layout does), so
     the paired image is staged; RECOIL_BATCH_NO_PAIRS stages the byte layout instead."""
     R = recoil_lib
@@ -199,6 +199,40 @@ def test_adaptive_paired_layout_staged_where_it_fits(recoil_lib):
     a, tables, s, tid = _case(20_000, 29, n_tables=4, alphabet=1000)
     p = R.encode_adaptive(s, 16, tables, tid, 64)
     assert R.Plan([p], {"warps_per_cta": 32}).kernels == R.KERNEL_ADAPTIVE16_WIDE
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("warps", [8, 32])
+def test_gpu_adaptive_long_and_short_synchronisation_phases(recoil_lib, warps):
+    """The groups a split decodes outside its steady loop read table numbers from blocks staged
+    beforehand (three blocks of 8 groups from the split's top group, and from where the steady
+    loop stops), else from global memory. A near-deterministic PDF (one symbol holds all but 255
+    slots: a coder reads a word every few hundred symbols) in long runs gives synchronisation
+    phases far longer than 24 groups; 3000 splits over 200 K symbols give splits of a few groups.
+    Both decode to the input and to the oracle's split decode, paired and byte layouts."""
+    R = recoil_lib
+    g = np.random.default_rng(61)
+    A, n, N = 256, 16, 200_003
+    tables = np.ones((3, A), dtype=np.uint32)
+    tables[0, 128] = (1 << n) - (A - 1)
+    tables[1, :] = (1 << n) // A
+    tables[2] = workloads.AdaptiveStream("t", 1, n_tables=3).tables()[1]
+    runs = g.integers(1, 4000, size=400)
+    tid = np.repeat(g.integers(0, 3, size=len(runs)), runs)[:N].astype(np.uint8)
+    tid = np.concatenate([tid, np.zeros(N - len(tid), np.uint8)])
+    cdf = np.cumsum(tables, axis=1) / float(1 << n)
+    s = np.array([np.searchsorted(cdf[t], u, side="right") for t, u in zip(tid, g.random(N))], dtype=np.uint16)
+    p = R.encode_adaptive(s, n, tables, tid, 3000)
+    o = oracle.encode_adaptive_with_splits(s, tid, tables, n, 3000)
+    idx = p.export()["entry_index"].astype(np.int64) // 32
+    assert (idx.max(1) - idx.min(1)).max() > 24            # phases beyond the three staged blocks
+    assert np.diff(np.sort(idx.max(1))).min() < 24          # splits shorter than the staged blocks
+    for flags in (R.BATCH_GRAPH, R.BATCH_NO_PAIRS):
+        for Mp in (3000, 300, 37):
+            c = R.combine_splits(p, Mp)
+            (out,) = _gpu_decode(R, [c], {"warps_per_cta": warps, "flags": flags})
+            assert np.array_equal(out, s), (flags, Mp)
+            assert np.array_equal(out, oracle.decode_splits(oracle.combined(o, Mp)).astype(out.dtype)), (flags, Mp)
 
 
 @pytest.mark.gpu
