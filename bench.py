@@ -477,6 +477,7 @@ def run_adaptive(a):
     enc = R.encode_adaptive(s, st.n_bits, tables, tid, max(1, min(65536, len(s) // 4096)))
     warps = a.warps                                    # 0: the library picks the CTA size
     lane_flag = R.BATCH_TWO_LANES if a.lanes == 2 else 0
+    layout_flag = 0                                    # the paired layout where the model has one
     cs = torch.cuda.Stream(device=dev)
     out = torch.empty(len(s) * 2, dtype=torch.uint8, device=dev)
     ref = torch.from_numpy(s.view(np.uint8)).to(dev)
@@ -512,9 +513,11 @@ def run_adaptive(a):
             best, tms = R.autotune([c], [out.data_ptr()], tws, tws.numel(), cs, steps=3, keep_splits=True)
             warps = best["warps_per_cta"]
             lane_flag = best["flags"] & R.BATCH_TWO_LANES
-            tuned = {"warps_per_cta": warps, "lanes_per_thread": 2 if lane_flag else 1, "ms": round(tms, 4)}
+            layout_flag = best["flags"] & R.BATCH_NO_PAIRS
+            tuned = {"warps_per_cta": warps, "lanes_per_thread": 2 if lane_flag else 1,
+                     "table_layout": "byte guide" if layout_flag else "paired", "ms": round(tms, 4)}
             del tws
-        plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag})
+        plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag | layout_flag})
         warps = plan.warps_per_cta
         ws = torch.empty(plan.workspace_size, dtype=torch.uint8, device=dev)
         plan.upload(ws, stream=cs)
@@ -533,7 +536,7 @@ def run_adaptive(a):
         e2e = None
         if not a.no_e2e:
             R.stream_pin(c)
-            pipe = R.Pipeline([c], {"warps_per_cta": warps, "split_symbols": 0, "flags": lane_flag},
+            pipe = R.Pipeline([c], {"warps_per_cta": warps, "split_symbols": 0, "flags": lane_flag | layout_flag},
                               groups=a.e2e_groups)
             wsb, stb = pipe.sizes
             pws = torch.empty(wsb, dtype=torch.uint8, device=dev)
@@ -560,15 +563,16 @@ def run_adaptive(a):
                                    f"Gaussian scale tables (0.11..256) over {a.alphabet} values, n=16, W=32",
                        "splits": c.info["n_entries"], "warps_per_cta": warps,
                        "lanes_per_thread": 2 if lane_flag else 1, "autotuned": tuned,
+                       "table_layout": "byte guide" if layout_flag or a.alphabet > 256 else "paired",
                        "symbols_bytes": out_bytes,
                        "compressed_bytes": 2 * c.info["n_words"] + 4 * 32, "table_number_bytes": len(s),
                        "l2": "inputs larger than L2 (no flush)", "scale": a.scale},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                          "traffic": (recorded_traffic(f"adaptive w{warps} k{a.splits} l{2 if lane_flag else 1}")
-                                     if a.scale == 1.0 and default_model else None),
+                                     if a.scale == 1.0 and default_model and not layout_flag else None),
                          "issue": (issue_rate(f"adaptive w{warps} k{a.splits} l{2 if lane_flag else 1}", mean_ms, dev, clocks)
-                                   if a.scale == 1.0 and default_model else None),
+                                   if a.scale == 1.0 and default_model and not layout_flag else None),
                          "peak_source": peaks["source"],
                          "kernel": "decode_kernel<kAdaptive16>" if a.alphabet <= 256 else "decode_kernel<kAdaptive16Wide>",
                          "bytes": "compressed words + table numbers in, symbols out"},
@@ -669,7 +673,7 @@ def configs_block(R, torch, dev, cs, scale: float, steps: int, warmup: int) -> d
             tws = torch.empty(R.autotune_workspace_size(streams), dtype=torch.uint8, device=dev)
             best, _ = R.autotune(streams, [out.data_ptr()], tws, tws.numel(), cs, steps=3, keep_splits=True)
             warps = best["warps_per_cta"]
-            lane_flag = best["flags"] & R.BATCH_TWO_LANES
+            lane_flag = best["flags"] & (R.BATCH_TWO_LANES | R.BATCH_NO_PAIRS)   # lanes and table layout
             del tws
         plan = R.Plan(streams, {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag})
         ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device=dev)
@@ -686,7 +690,7 @@ def configs_block(R, torch, dev, cs, scale: float, steps: int, warmup: int) -> d
         words = sum(2 * st.info["n_words"] + 4 * 32 for st in streams)
         t = statistics.mean(ms) * 1e-3
         r = {"gbs": round(nbytes / t / 1e9, 1), "us": round(t * 1e6, 1), "warps_per_cta": plan.warps_per_cta,
-             "lanes_per_thread": 2 if lane_flag else 1,
+             "lanes_per_thread": 2 if lane_flag & R.BATCH_TWO_LANES else 1,
              "splits": sum(st.info["n_entries"] for st in streams),
              "frac": round((nbytes + words + extra_in) / t / 1e9 / peak, 4), "exact": exact}
         del ws

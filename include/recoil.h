@@ -471,16 +471,22 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
 /*
  * Choose batch options for these streams by measurement (the batching pattern
  * of the paper's decoder-adaptive parallelism, Sec. 3.3: the decoder picks the
- * split count that suits it). Candidates: warps_per_cta in {4, 8, 16} (and 32
- * when a stream is adaptive) times split_symbols in {32 Ki, 64 Ki, 128 Ki,
- * 256 Ki} (with RECOIL_TUNE_KEEP_SPLITS: those warps_per_cta on the streams as
- * given, split_symbols 0, for a
- * decoder whose split count is already chosen). Each candidate decodes the
- * streams into d_outs (caller-owned, as for recoil_plan_decode) once untimed
- * and `steps` times timed with CUDA events on cuda_stream; the lowest median
- * wins and is written to *best (ctas_per_sm = 0, flags = 0) with its time in
+ * split count that suits it). Candidates: coder lanes a thread (one, or two
+ * with RECOIL_BATCH_TWO_LANES) times the warps_per_cta built for that and for
+ * every kind in the batch (one lane: 4, 8, 16, and 32 when a stream is
+ * adaptive; two lanes: 4, 8, 16 static, 8, 16, 24 adaptive) times
+ * split_symbols in {32 Ki, 64 Ki, 128 Ki, 256 Ki} (with
+ * RECOIL_TUNE_KEEP_SPLITS: split_symbols 0, the streams as given, for a
+ * decoder whose split count is already chosen), and, when an adaptive model
+ * has at most 256 symbols, both table layouts (paired, or the one-byte guide
+ * with RECOIL_BATCH_NO_PAIRS). Each candidate decodes the streams into d_outs
+ * (caller-owned, as for recoil_plan_decode) once untimed and `steps` times
+ * timed with CUDA events on cuda_stream; the lowest median wins and is
+ * written to *best (ctas_per_sm = 0; flags: the winner's
+ * RECOIL_BATCH_TWO_LANES and RECOIL_BATCH_NO_PAIRS bits) with its time in
  * *best_ms (may be NULL). With a cache_path, a result cached for the same GPU
- * and batch shape is returned without decoding, and new results are appended.
+ * and batch shape is returned without decoding, and new results are appended
+ * (one line: key, warps, split symbols, lanes, layout 0 or 1, ms).
  * d_workspace: >= recoil_autotune_workspace_size bytes, 256-byte aligned.
  * Synchronises cuda_stream. Errors: EINVAL, ENOMEM (workspace too small),
  * ECORRUPT, ECUDA.

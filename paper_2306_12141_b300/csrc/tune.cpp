@@ -1,6 +1,8 @@
 // Autotuner for batched decoding: picks coder lanes a thread (one split a
-// warp, or two in lockstep), warps per CTA and the split size a batch is
-// combined to by timing each candidate on the caller's own streams.
+// warp, or two in lockstep), warps per CTA, the split size a batch is
+// combined to and, for adaptive models over up to 256 symbols, which table
+// layout is staged (paired or one-byte guide), by timing each candidate on
+// the caller's own streams.
 //
 // Candidates differ only in how streams are split, so they share the bulk of
 // the device image (words and tables): it is uploaded once and each candidate
@@ -26,21 +28,25 @@ const uint32_t kSplit[] = {32768, 65536, 131072, 262144};
 
 // Candidate options: lanes a thread (1 or 2) x warps x split sizes, or lanes
 // x warps alone on the streams' own splits, every shape a kernel is built for
-// with each kind in the batch. 32-warp CTAs only for adaptive streams (one
-// CTA an SM leaves room for the finer guide); static kinds keep 4 to 16.
-std::vector<recoil_batch_opts> candidates(bool keep_splits, bool has_static, bool has_adaptive) {
+// with each kind in the batch, and both table layouts where an adaptive
+// model has the paired one. 32-warp CTAs only for adaptive streams (one CTA
+// an SM leaves room for the finer guide); static kinds keep 4 to 16.
+std::vector<recoil_batch_opts> candidates(bool keep_splits, bool has_static, bool has_adaptive, bool pairable) {
   std::vector<recoil_batch_opts> c;
-  for (uint32_t lanes : {1u, 2u}) {
-    for (uint32_t w : kWarps) {
-      if (has_static && !shape_supported(false, w, lanes)) continue;
-      if (has_adaptive && !shape_supported(true, w, lanes)) continue;
-      if (lanes == 1 && w == 32 && !has_adaptive) continue;
-      const uint32_t flags = lanes == 2 ? RECOIL_BATCH_TWO_LANES : 0;
-      if (keep_splits) {
-        c.push_back(recoil_batch_opts{w, 0, 0, flags});
-        continue;
+  for (uint32_t layout : {0u, RECOIL_BATCH_NO_PAIRS}) {
+    if (layout && !pairable) continue;
+    for (uint32_t lanes : {1u, 2u}) {
+      for (uint32_t w : kWarps) {
+        if (has_static && !shape_supported(false, w, lanes)) continue;
+        if (has_adaptive && !shape_supported(true, w, lanes)) continue;
+        if (lanes == 1 && w == 32 && !has_adaptive) continue;
+        const uint32_t flags = (lanes == 2 ? RECOIL_BATCH_TWO_LANES : 0) | layout;
+        if (keep_splits) {
+          c.push_back(recoil_batch_opts{w, 0, 0, flags});
+          continue;
+        }
+        for (uint32_t sp : kSplit) c.push_back(recoil_batch_opts{w, 0, sp, flags});
       }
-      for (uint32_t sp : kSplit) c.push_back(recoil_batch_opts{w, 0, sp, flags});
     }
   }
   return c;
@@ -68,7 +74,9 @@ std::string tune_key(const recoil_stream* const* s, uint32_t count) {
   return k.str();
 }
 
-// Cache lines: key, warps, split symbols, lanes a thread, time (ms).
+// Cache lines: key, warps, split symbols, lanes a thread, table layout (0:
+// paired where a model has it, 1: one-byte guide), time (ms). Lines without
+// the layout field read as layout 0.
 bool cache_lookup(const char* path, const std::string& key, recoil_batch_opts* best, float* ms) {
   if (!path) return false;
   std::ifstream f(path);
@@ -77,12 +85,18 @@ bool cache_lookup(const char* path, const std::string& key, recoil_batch_opts* b
   while (std::getline(f, line)) {
     std::istringstream in(line);
     std::string k;
-    uint32_t w = 0, sp = 0, lanes = 0;
-    float t = 0;
-    if (in >> k >> w >> sp >> lanes >> t && k == key && (lanes == 1 || lanes == 2) &&
+    std::vector<double> v;
+    double x = 0;
+    if (!(in >> k) || k != key) continue;
+    while (in >> x) v.push_back(x);
+    if (v.size() != 4 && v.size() != 5) continue;
+    const uint32_t w = (uint32_t)v[0], sp = (uint32_t)v[1], lanes = (uint32_t)v[2];
+    const uint32_t layout = v.size() == 5 ? (uint32_t)v[3] : 0u;
+    if ((lanes == 1 || lanes == 2) && layout <= 1 &&
         (lanes == 2 ? (w == 4 || w == 8 || w == 16 || w == 24) : warps_supported(w))) {
-      *best = recoil_batch_opts{w, 0, sp, lanes == 2 ? RECOIL_BATCH_TWO_LANES : 0u};
-      *ms = t;
+      *best = recoil_batch_opts{w, 0, sp, (lanes == 2 ? RECOIL_BATCH_TWO_LANES : 0u) |
+                                              (layout ? RECOIL_BATCH_NO_PAIRS : 0u)};
+      *ms = (float)v.back();
       hit = true;                          // the last line for a key wins
     }
   }
@@ -93,7 +107,8 @@ void cache_store(const char* path, const std::string& key, const recoil_batch_op
   if (!path) return;
   std::ofstream f(path, std::ios::app);
   f << key << ' ' << b.warps_per_cta << ' ' << b.split_symbols << ' '
-    << ((b.flags & RECOIL_BATCH_TWO_LANES) ? 2 : 1) << ' ' << ms << '\n';
+    << ((b.flags & RECOIL_BATCH_TWO_LANES) ? 2 : 1) << ' ' << ((b.flags & RECOIL_BATCH_NO_PAIRS) ? 1 : 0) << ' '
+    << ms << '\n';
 }
 
 struct Candidate {
@@ -113,6 +128,13 @@ bool any_static(const recoil_stream* const* s, uint32_t count) {
   return false;
 }
 
+// An adaptive model with the paired layout (one-byte guide entries: up to 256 symbols).
+bool any_pairable(const recoil_stream* const* s, uint32_t count) {
+  for (uint32_t i = 0; i < count; i++)
+    if (s && s[i] && s[i]->adaptive() && s[i]->alphabet() <= 256) return true;
+  return false;
+}
+
 }  // namespace
 }  // namespace recoil
 
@@ -125,7 +147,8 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
   if (!bytes) return fail(RECOIL_EINVAL, "null argument");
   size_t mx = 0;
   for (bool keep : {false, true})
-    for (recoil_batch_opts o : candidates(keep, any_static(streams, count), any_adaptive(streams, count))) {
+    for (recoil_batch_opts o :
+         candidates(keep, any_static(streams, count), any_adaptive(streams, count), any_pairable(streams, count))) {
       size_t b = 0;
       int rc = recoil_workspace_size(streams, count, &o, &b);
       if (rc) return rc;
@@ -158,7 +181,8 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
     for (Candidate& c : cands) recoil_plan_free(c.plan);
   };
   size_t bulk = 0;
-  for (const recoil_batch_opts& o : candidates(keep, any_static(streams, count), any_adaptive(streams, count))) {
+  for (const recoil_batch_opts& o :
+       candidates(keep, any_static(streams, count), any_adaptive(streams, count), any_pairable(streams, count))) {
     Candidate c;
     c.opts = o;
     int rc = recoil_plan_create(streams, count, &c.opts, &c.plan);

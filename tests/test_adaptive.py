@@ -410,6 +410,38 @@ def test_gpu_adaptive_in_serving_pipeline_and_autotune(recoil_lib, tmp_path):
 
 
 @pytest.mark.gpu
+def test_gpu_autotune_chooses_the_table_layout(recoil_lib, tmp_path):
+    """Adaptive models over up to 256 symbols give the autotuner both table layouts (paired and
+    one-byte guide): its cache line records the layout it chose, a cached byte-guide line comes
+    back with RECOIL_BATCH_NO_PAIRS (the plan then stages the byte layout) and a paired one
+    without, and every choice decodes to the input."""
+    import torch
+    R = recoil_lib
+    a, tables, s, tid = _case(300_007, 31)
+    p = R.combine_splits(R.encode_adaptive(s, 16, tables, tid, 512), 296)
+    need = R.autotune_workspace_size([p])
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(len(s) * 2, dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.current_stream()
+    cache = str(tmp_path / "tune.txt")
+    best, ms = R.autotune([p], [out.data_ptr()], ws, need, cs, steps=2, cache_path=cache, keep_splits=True)
+    assert ms > 0 and np.array_equal(out.cpu().numpy().view(np.uint16), s)
+    key, w, sp, lanes, layout, t = open(cache).read().split("\n")[0].split()
+    assert layout in ("0", "1") and (layout == "1") == bool(best["flags"] & R.BATCH_NO_PAIRS)
+    chosen = {}
+    for lay, kernel in (("1", R.KERNEL_ADAPTIVE16), ("0", R.KERNEL_ADAPTIVE16_PAIR)):
+        with open(cache, "a") as f:
+            f.write(f"{key} 32 0 1 {lay} {t}\n")
+        got, _ = R.autotune([p], [out.data_ptr()], ws, need, cs, cache_path=cache, keep_splits=True)
+        assert got["warps_per_cta"] == 32 and bool(got["flags"] & R.BATCH_NO_PAIRS) == (lay == "1")
+        assert R.Plan([p], got).kernels == kernel
+        chosen[lay] = got
+    for opts in (best, *chosen.values()):
+        (o,) = _gpu_decode(R, [p], opts)
+        assert np.array_equal(o, s), opts
+
+
+@pytest.mark.gpu
 def test_gpu_adaptive_corrupt_words_flagged(recoil_lib):
     """Words flipped in the uploaded device image of an adaptive stream are reported by
     the decoders' state cross-check (no fault, no hang), and the context stays usable."""

@@ -336,17 +336,23 @@ def test_autotune_chooses_a_working_configuration(recoil_lib, tmp_path):
     assert keep["warps_per_cta"] in (4, 8, 16) and keep["split_symbols"] == 0 and ms3 > 0
     for s, out in zip(syms, gpu_decode(R, streams, keep)):
         assert np.array_equal(out, s)
-    # cache lines carry the lanes a thread: key, warps, split symbols, lanes, ms; the last line of a
-    # key wins, so an appended two-lane line is what the next lookup returns
+    # cache lines carry the lanes a thread and the table layout: key, warps, split symbols, lanes,
+    # layout, ms (a line without the layout reads as layout 0); the last line of a key wins, so an
+    # appended two-lane line is what the next lookup returns
     lines = open(cache).read().split("\n")
-    key, w, sp, lanes, t = lines[0].split()
+    key, w, sp, lanes, layout, t = lines[0].split()
     assert lanes in ("1", "2") and int(w) == best["warps_per_cta"] and int(sp) == best["split_symbols"]
+    assert layout == "0"                                          # static streams have one layout
     with open(cache, "a") as f:
-        f.write(f"{key} 8 65536 2 {t}\n")
+        f.write(f"{key} 8 65536 2 0 {t}\n")
     two, _ = R.autotune(streams, ptrs, ws, need, cs, cache_path=cache)
     assert two["warps_per_cta"] == 8 and two["split_symbols"] == 65536 and two["flags"] & R.BATCH_TWO_LANES
     for s, out in zip(syms, gpu_decode(R, streams, two)):
         assert np.array_equal(out, s)
+    with open(cache, "a") as f:
+        f.write(f"{key} 16 32768 1 {t}\n")
+    old, _ = R.autotune(streams, ptrs, ws, need, cs, cache_path=cache)
+    assert old["warps_per_cta"] == 16 and old["split_symbols"] == 32768 and old["flags"] == 0
 
 
 def test_pipeline_decodes_host_to_host(recoil_lib):
