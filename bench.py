@@ -586,17 +586,23 @@ def run_adaptive(a):
     print(json.dumps(line), flush=True)
 
 
-def time_events(fn, cs, steps: int, warmup: int) -> list[float]:
-    """Milliseconds of each of `steps` calls of fn, CUDA events on cs, after `warmup` calls."""
+def time_events(fn, cs, steps: int, warmup: int, gate_ms: float = 2.0) -> list[float]:
+    """Milliseconds of each of `steps` calls of fn, CUDA events on cs, after `warmup` calls. The
+    timed calls are queued behind a short device-side sleep (gate_ms, untimed), so the device runs
+    them back to back and a host scheduling delay while they are queued cannot enter an event pair
+    (it would dominate decodes of tens of microseconds)."""
     import torch
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for e0, e1 in ev:
-        e0.record(cs)
-        fn()
-        e1.record(cs)
+    with torch.cuda.stream(cs):
+        if gate_ms > 0:
+            torch.cuda._sleep(int(gate_ms * 1e-3 * 2.0e9))   # ~gate_ms at the B300's 2 GHz SM clock
+        for e0, e1 in ev:
+            e0.record(cs)
+            fn()
+            e1.record(cs)
     torch.cuda.synchronize()
     return [e0.elapsed_time(e1) for e0, e1 in ev]
 
@@ -627,7 +633,7 @@ def per_stream_round_robin(R, torch, dev, streams, out_ptrs, warps: int, split_s
             done.record(c)
             main.wait_event(done)
 
-    ms = time_events(step, main, steps, 1)
+    ms = time_events(step, main, steps, 1, gate_ms=0)   # the launches' host cost is part of this baseline
     errors = sum(p.errors(c) for p, c in zip(plans, side))
     assert errors == 0, R.recoil_last_error()
     return {"ms_per_step": statistics.mean(ms), "launches_per_step": sum(p.launches for p in plans),
