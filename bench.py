@@ -597,8 +597,9 @@ def time_events(fn, cs, steps: int, warmup: int, gate_ms: float = 2.0) -> list[f
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(cs):
-        if gate_ms > 0:
-            torch.cuda._sleep(int(gate_ms * 1e-3 * 2.0e9))   # ~gate_ms at the B300's 2 GHz SM clock
+        sleep = getattr(torch.cuda, "_sleep", None)          # torch's bounded spin kernel (clock cycles)
+        if gate_ms > 0 and sleep is not None:
+            sleep(int(gate_ms * 1e-3 * 2.0e9))                # ~gate_ms at the B300's 2 GHz SM clock
         for e0, e1 in ev:
             e0.record(cs)
             fn()
