@@ -425,7 +425,8 @@ typedef struct {
   uint32_t max_inflight;     /* most launches seen on the device at once */
 } recoil_serve_stats;
 
-/* Arena bytes recoil_serve needs: resident pool words and tables, one
+/* Arena bytes recoil_serve needs: resident pool words, tables and split
+ * descriptors (every entry of every pool stream, 288 bytes each), one
  * descriptor area per launch slot, and the output budget. */
 int recoil_serve_arena_size(const recoil_stream* const* pool, uint32_t pool_count, const recoil_serve_opts* opts,
                             size_t* bytes);

@@ -7,7 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librecoil.so")
-SOURCES = ["decode_kernels.cu", "plan.cpp", "host_codec.cpp", "tune.cpp", "serve.cpp", "pipeline.cpp", "serialize.cpp", "noalloc.cu"]
+SOURCES = ["decode_kernels.cu", "plan.cpp", "host_codec.cpp", "tune.cpp", "serve.cpp", "serve_kernels.cu", "pipeline.cpp",
+           "serialize.cpp", "noalloc.cu"]
 HEADERS = ["recoil_internal.h", "device_types.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

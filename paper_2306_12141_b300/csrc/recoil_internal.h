@@ -94,6 +94,19 @@ void plan_kernel_outs(const recoil_plan* plan, void* const* outs, void** dev);
 // sits at the start of the workspace: plan_bulk_bytes bytes written to dst.
 void plan_bulk_image(const recoil_plan* plan, uint8_t* dst);
 
+// Serving (serve_kernels.cu): a kept split of an admission as a reference to
+// a resident pool descriptor, with the owned low end and the stream index the
+// admission gives it; the device expands the references into descriptors.
+struct EntryRef {
+  uint32_t src;              // index of the descriptor in the resident pool set
+  uint32_t lo;               // first owned symbol (the previous kept split's end)
+  uint32_t stream;           // the request's place among the launch's streams
+  uint32_t pad;
+};
+static_assert(sizeof(EntryRef) == 16, "EntryRef layout");
+cudaError_t launch_expand_entries(const DevEntry* pool, const EntryRef* refs, DevEntry* out, uint32_t n,
+                                  cudaStream_t s);
+
 // Error reporting (thread-local message).
 int fail(int code, const std::string& msg);
 void clear_error();

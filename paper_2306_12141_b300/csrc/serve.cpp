@@ -10,9 +10,11 @@
 //   - combines each admitted stream to its share of the warp slots that are
 //     free at that moment (Sec. 3.3: the decoder's parallelism decides the
 //     split count) by picking entries of the pool stream, whose descriptors
-//     are built once for the whole pool before the run, copies them to
-//     the slot's descriptor area and launches one persistent decode for the
-//     whole admission on the slot's own CUDA stream,
+//     are built and made resident once for the whole pool before the run,
+//     sends one 16-byte reference per kept split to the slot's descriptor
+//     area, expands them there into descriptors on the device and launches
+//     one persistent decode for the whole admission on the slot's own CUDA
+//     stream,
 // so requests that arrive while others run are admitted as memory and slots
 // free up, and their decodes overlap on the device. Latency is arrival to the
 // device completion of the launch that carried the request.
@@ -23,11 +25,15 @@
 // All waits are bounded by opts->timeout_s (host wall clock); kernels have no
 // waits of their own.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -44,11 +50,97 @@ constexpr size_t kAlign = 256;
 // but with p99 outliers above 1 ms at 10k-20k req/s; 16 MiB / 8x kept.
 constexpr size_t kDefaultMeta = (size_t)16 << 20;
 constexpr size_t kBacklogBatches = 8;   // admission size under a backlog, in max_batch
+// Admissions of at least this many requests build their descriptors on
+// kBuildThreads more host threads (at a saturating load the serving thread
+// spent most of its time there).
+constexpr size_t kParallelRequests = 64;
+constexpr unsigned kBuildThreads = 6;
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 double now_s() {
   using C = std::chrono::steady_clock;
   return std::chrono::duration<double>(C::now().time_since_epoch()).count();
+}
+
+// Host threads that build a large admission's descriptors together with the
+// serving thread: run(count, f) calls f(begin, end) on disjoint chunks of
+// [0, count) and returns when all are done. The workers sleep between calls.
+class Workers {
+ public:
+  explicit Workers(unsigned n) {
+    try {
+      for (unsigned i = 0; i < n; i++) threads_.emplace_back([this] { loop(); });
+    } catch (...) {                                   // fewer threads (or none): run() still works
+    }
+  }
+  ~Workers() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+      gen_++;
+    }
+    cv_.notify_all();
+    for (std::thread& t : threads_) t.join();
+  }
+  void run(size_t count, const std::function<void(size_t, size_t)>& f) {
+    if (threads_.empty() || count < 2) {
+      if (count) f(0, count);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      job_ = &f;
+      total_ = count;
+      chunk_ = std::max<size_t>(1, count / (4 * (threads_.size() + 1)));
+      next_.store(0);
+      pending_ = threads_.size();
+      gen_++;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(mu_);
+    done_.wait(g, [this] { return pending_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  void work() {
+    for (;;) {
+      const size_t b = next_.fetch_add(chunk_);
+      if (b >= total_) return;
+      (*job_)(b, std::min(b + chunk_, total_));
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (stop_) return;
+      }
+      work();
+      std::lock_guard<std::mutex> g(mu_);
+      if (--pending_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(size_t, size_t)>* job_ = nullptr;
+  size_t total_ = 0, chunk_ = 1, pending_ = 0;
+  std::atomic<size_t> next_{0};
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+// Bytes of the resident descriptor set: every entry of every pool stream and
+// its final-state entry.
+size_t pool_desc_bytes(const recoil_stream* const* pool, uint32_t pool_count) {
+  uint64_t n = 0;
+  for (uint32_t i = 0; i < pool_count; i++) n += pool[i]->entries.size() + 1;
+  return align_up(n * sizeof(DevEntry), kAlign);
 }
 
 // First-fit allocator over [0, size) of the output heap (offsets only).
@@ -124,7 +216,8 @@ int recoil_serve_arena_size(const recoil_stream* const* pool, uint32_t pool_coun
   recoil_plan_free(P);
   const uint32_t slots = opts->max_inflight ? opts->max_inflight : 8;
   const size_t meta = opts->meta_bytes ? opts->meta_bytes : kDefaultMeta;
-  *bytes = align_up(bulk, kAlign) + slots * align_up(meta, kAlign) + align_up(opts->budget_bytes, kAlign);
+  *bytes = align_up(bulk, kAlign) + pool_desc_bytes(pool, pool_count) + slots * align_up(meta, kAlign) +
+           align_up(opts->budget_bytes, kAlign);
   return RECOIL_OK;
 }
 
@@ -155,7 +248,8 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   PlanImage img;
   plan_image(poolplan, &img);
   const size_t bulk = align_up(plan_bulk_bytes(poolplan), kAlign);
-  const size_t need = bulk + nslots * meta_cap + (d_req_outs ? 0 : align_up(opts->budget_bytes, kAlign));
+  const size_t descs = pool_desc_bytes(pool, pool_count);
+  const size_t need = bulk + descs + nslots * meta_cap + (d_req_outs ? 0 : align_up(opts->budget_bytes, kAlign));
   if (arena_bytes < need) return fail(RECOIL_ENOMEM, "arena smaller than recoil_serve_arena_size");
   if (((uintptr_t)d_arena) % kAlign) return fail(RECOIL_EINVAL, "arena must be 256-byte aligned");
   uint8_t* arena = (uint8_t*)d_arena;
@@ -189,7 +283,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
     e = cudaStreamCreateWithFlags(&slots[i].stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&slots[i].done);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&slots[i].host, meta_cap + sizeof(DevControl), cudaHostAllocDefault);
-    slots[i].dev = arena + bulk + i * meta_cap;
+    slots[i].dev = arena + bulk + descs + i * meta_cap;
   }
   if (e == cudaSuccess) e = cudaEventCreate(&t0ev);
   if (e == cudaSuccess) rc = plan_upload_parts(poolplan, arena, arena_bytes, slots[0].stream, true, false);
@@ -198,7 +292,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
     cleanup();
     return rc ? rc : fail(RECOIL_ECUDA, std::string("serve setup: ") + cudaGetErrorString(e));
   }
-  uint8_t* heap_base = arena + bulk + nslots * meta_cap;
+  uint8_t* heap_base = arena + bulk + descs + nslots * meta_cap;
   Heap heap(d_req_outs ? 0 : opts->budget_bytes);
   size_t budget_used = 0;                         // with caller outputs: bytes of admitted outputs
   std::vector<size_t> out_bytes(n_req);
@@ -211,15 +305,43 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
     }
   }
 
-  // every entry descriptor of every pool stream, built once like the resident
-  // words (a server prepares its content before it takes requests)
-  std::vector<std::vector<DevEntry>> pool_ents(pool_count);
-  try {
-    for (uint32_t i = 0; i < pool_count; i++) build_entries(*pool[i], 0, pool_ents[i]);
-  } catch (const std::bad_alloc&) {
-    cleanup();
-    return fail(RECOIL_ENOMEM, "host allocation failed");
+  // every entry descriptor of every pool stream, built once and made resident
+  // like the words (a server prepares its content before it takes requests);
+  // pool stream i's descriptors start at pool_first[i], its final-state entry last
+  std::vector<uint64_t> pool_first(pool_count + 1, 0);
+  std::vector<uint32_t> pool_hi1;                        // each resident descriptor's owned end
+  {
+    std::vector<DevEntry> flat, one;
+    try {
+      for (uint32_t i = 0; i < pool_count; i++) {
+        one.clear();                                       // build_entries appends
+        build_entries(*pool[i], 0, one);
+        pool_first[i] = flat.size();
+        flat.insert(flat.end(), one.begin(), one.end());
+      }
+    } catch (const std::bad_alloc&) {
+      cleanup();
+      return fail(RECOIL_ENOMEM, "host allocation failed");
+    }
+    pool_first[pool_count] = flat.size();
+    if (flat.size() > 0xffffffffull) {
+      cleanup();
+      return fail(RECOIL_EINVAL, "the pool holds more than 2^32 split descriptors");
+    }
+    try {
+      pool_hi1.resize(flat.size());
+    } catch (const std::bad_alloc&) {
+      cleanup();
+      return fail(RECOIL_ENOMEM, "host allocation failed");
+    }
+    for (size_t x = 0; x < flat.size(); x++) pool_hi1[x] = flat[x].hi1;
+    e = cudaMemcpy(arena + bulk, flat.data(), flat.size() * sizeof(DevEntry), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cleanup();
+      return fail(RECOIL_ECUDA, std::string("serve setup: ") + cudaGetErrorString(e));
+    }
   }
+  const DevEntry* pool_dev = reinterpret_cast<const DevEntry*>(arena + bulk);
 
   // the run clock: host t0 and a device event recorded at the same moment
   e = cudaEventRecord(t0ev, slots[0].stream);
@@ -229,17 +351,12 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   uint32_t warps_busy = 0;
   double first_arrival = n_req ? req_arrival_s[0] : 0.0, last_done = 0.0;
   uint64_t sym_bytes_total = 0;
-  // an admitted split: its descriptor in the pool set, its owned low end and
-  // its request's place in the launch
-  struct EntRef {
-    const DevEntry* src;
-    uint32_t lo;
-    uint32_t stream;
-  };
-  std::vector<EntRef> ents;
   std::vector<DevItem> items;
   std::vector<uint32_t> item_kind;
-  std::vector<uint32_t> keep;
+  std::vector<std::vector<uint32_t>> keeps;     // per admitted request: its kept regular entries
+  std::vector<size_t> ent_first;                // per admitted request: its first descriptor
+  // large admissions (a backlog) build their descriptors on a few more host threads
+  Workers workers(per_request ? 0u : std::min(kBuildThreads, std::max(1u, std::thread::hardware_concurrency()) - 1));
   int status = RECOIL_OK;
 
   while (done < n_req && e == cudaSuccess && status == RECOIL_OK) {
@@ -304,7 +421,8 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
       uint64_t sum_entries = 0, sum_share = free_w0;
       auto meta_bound = [&](size_t n, uint64_t ents_max) {
         return sizeof(DevControl) + align_up(n * 8, kAlign) + align_up(n * sizeof(DevStream), kAlign) +
-               align_up(ents_max * sizeof(DevItem), kAlign) + ents_max * sizeof(DevEntry);
+               align_up(ents_max * sizeof(DevItem), kAlign) + align_up(ents_max * sizeof(EntryRef), kAlign) +
+               ents_max * sizeof(DevEntry);
       };
       while (next < n_req && req_arrival_s[next] <= t && sl.reqs.size() < cap_n) {
         const uint32_t r = next;
@@ -336,55 +454,62 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
         const size_t off_outs = sizeof(DevControl);
         const size_t off_streams = off_outs + align_up(n * 8, kAlign);
         const size_t off_items = off_streams + align_up(n * sizeof(DevStream), kAlign);
-        ents.clear();
+        if (keeps.size() < n) keeps.resize(n);
+        ent_first.resize(n + 1);
+        // each request's kept entries (combine, Sec. 3.3, without building a
+        // combined stream: the picks index the pool stream's descriptors)
+        const std::function<void(size_t, size_t)> pick = [&](size_t b, size_t end) {
+          for (size_t k = b; k < end; k++) {
+            const recoil_stream* src = pool[req_stream[sl.reqs[k]]];
+            uint32_t target = (uint32_t)src->entries.size() + 1;
+            if (!per_request) {
+              // the request's share of the free warps, but splits no longer than
+              // max_split: a split is one warp's sequential work
+              const double share = syms_batch ? (double)src->n_syms / (double)syms_batch : 1.0;
+              uint64_t want = (uint64_t)std::max(1.0, std::floor(free_w * share));
+              want = std::max<uint64_t>(want, (src->n_syms + max_split - 1) / max_split);
+              want = (want + warps - 1) / warps * warps;
+              target = (uint32_t)std::min<uint64_t>(target, want);
+            }
+            combine_picks(*src, target, keeps[k]);
+          }
+        };
+        if (n >= kParallelRequests) workers.run(n, pick);
+        else pick(0, n);
         items.clear();
         item_kind.clear();
         uint32_t warps_launch = 0;
         std::vector<DevStream> ds(n);
         std::vector<void*> outp(n);
+        size_t n_ents = 0;
         for (size_t k = 0; k < n; k++) {
           const uint32_t r = sl.reqs[k];
           const recoil_stream* src = pool[req_stream[r]];
-          uint32_t target = (uint32_t)src->entries.size() + 1;
-          if (!per_request) {
-            // the request's share of the free warps, but splits no longer than
-            // max_split: a split is one warp's sequential work
-            const double share = syms_batch ? (double)src->n_syms / (double)syms_batch : 1.0;
-            uint64_t want = (uint64_t)std::max(1.0, std::floor(free_w * share));
-            want = std::max<uint64_t>(want, (src->n_syms + max_split - 1) / max_split);
-            want = (want + warps - 1) / warps * warps;
-            target = (uint32_t)std::min<uint64_t>(target, want);
-          }
-          // combine (Sec. 3.3) without building a combined stream: the kept
-          // entries' descriptors come from the pool stream's full set, each
-          // owning from the previous kept entry's end
-          const std::vector<DevEntry>& full = pool_ents[req_stream[r]];
-          combine_picks(*src, target, keep);
-          const size_t first = ents.size();
-          uint32_t prev_end = 0;
-          for (uint32_t pick : keep) {
-            ents.push_back(EntRef{&full[pick], prev_end, (uint32_t)k});
-            prev_end = full[pick].hi1;
-          }
-          ents.push_back(EntRef{&full.back(), prev_end, (uint32_t)k});   // the final-state entry
-          results[r].splits = (uint32_t)(ents.size() - first);
+          const size_t first = n_ents, count = keeps[k].size() + 1;     // kept entries and the final one
+          ent_first[k] = first;
+          n_ents += count;
+          results[r].splits = (uint32_t)count;
           results[r].launch = launches;
           ds[k] = pool_ds[req_stream[r]];
           outp[k] = d_req_outs ? d_req_outs[r] : (void*)(heap_base + sl.out_off[k]);
-          for (size_t x = first; x < ents.size(); x += warps) {
+          for (size_t x = first; x < n_ents; x += warps) {
             DevItem it;
             it.stream = (uint32_t)k;
             it.entry = (uint32_t)x;
-            it.count = (uint32_t)std::min<size_t>(warps, ents.size() - x);
-            it.work = (uint32_t)std::min<uint64_t>(src->n_syms / (keep.size() + 1), 0x7fffffff);
+            it.count = (uint32_t)std::min<size_t>(warps, n_ents - x);
+            it.work = (uint32_t)std::min<uint64_t>(src->n_syms / count, 0x7fffffff);
             items.push_back(it);
             item_kind.push_back(ds[k].kind);
           }
         }
-        if (status != RECOIL_OK) break;
-        const size_t off_entries = off_items + align_up(items.size() * sizeof(DevItem), kAlign);
-        const size_t meta_bytes = off_entries + ents.size() * sizeof(DevEntry);
-        if (meta_bytes > meta_cap) {
+        ent_first[n] = n_ents;
+        // the area: control, output pointers, streams, items, the split
+        // references (all copied from the host), then the descriptors the
+        // device expands from the references
+        const size_t off_refs = off_items + align_up(items.size() * sizeof(DevItem), kAlign);
+        const size_t off_entries = off_refs + align_up(n_ents * sizeof(EntryRef), kAlign);
+        const size_t meta_bytes = off_refs + n_ents * sizeof(EntryRef);
+        if (off_entries + n_ents * sizeof(DevEntry) > meta_cap) {
           status = fail(RECOIL_ENOMEM, "descriptors of one admission exceed meta_bytes; raise it or lower max_batch");
           break;
         }
@@ -396,7 +521,7 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
           return items[a].work > items[b].work;
         });
         uint8_t* h = sl.host;
-        std::memset(h, 0, off_entries);                     // control (queue heads, flags) starts at zero
+        std::memset(h, 0, off_refs);                        // control (queue heads, flags) starts at zero
         std::memcpy(h + off_outs, outp.data(), n * 8);
         std::memcpy(h + off_streams, ds.data(), n * sizeof(DevStream));
         DevItem* hi = reinterpret_cast<DevItem*>(h + off_items);
@@ -407,13 +532,28 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
           if (!kind_count[k]) kind_first[k] = x;
           kind_count[k]++;
         }
-        DevEntry* he = reinterpret_cast<DevEntry*>(h + off_entries);
-        for (size_t x = 0; x < ents.size(); x++) {             // one copy, pool descriptor to staging
-          he[x] = *ents[x].src;
-          he[x].lo = ents[x].lo;
-          he[x].stream = ents[x].stream;
-        }
+        // a reference per kept split into the staging area, each owning from
+        // the previous kept split's end
+        EntryRef* hr = reinterpret_cast<EntryRef*>(h + off_refs);
+        const std::function<void(size_t, size_t)> copy = [&](size_t b, size_t end) {
+          for (size_t k = b; k < end; k++) {
+            const uint64_t base = pool_first[req_stream[sl.reqs[k]]];
+            const uint64_t last = pool_first[req_stream[sl.reqs[k]] + 1] - 1;   // the final-state entry
+            EntryRef* d = hr + ent_first[k];
+            uint32_t prev_end = 0;
+            for (uint32_t pk : keeps[k]) {
+              *d++ = EntryRef{(uint32_t)(base + pk), prev_end, (uint32_t)k, 0};
+              prev_end = pool_hi1[base + pk];
+            }
+            *d = EntryRef{(uint32_t)last, prev_end, (uint32_t)k, 0};
+          }
+        };
+        if (n >= kParallelRequests) workers.run(n, copy);
+        else copy(0, n);
         e = cudaMemcpyAsync(sl.dev, h, meta_bytes, cudaMemcpyHostToDevice, sl.stream);
+        if (e == cudaSuccess)
+          e = launch_expand_entries(pool_dev, reinterpret_cast<const EntryRef*>(sl.dev + off_refs),
+                                    reinterpret_cast<DevEntry*>(sl.dev + off_entries), (uint32_t)n_ents, sl.stream);
         LaunchArgs a{};
         a.streams = reinterpret_cast<const DevStream*>(sl.dev + off_streams);
         a.entries = reinterpret_cast<const DevEntry*>(sl.dev + off_entries);
