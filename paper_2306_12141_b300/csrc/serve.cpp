@@ -25,15 +25,11 @@
 // All waits are bounded by opts->timeout_s (host wall clock); kernels have no
 // waits of their own.
 #include <algorithm>
-#include <atomic>
 #include <chrono>
 #include <cmath>
-#include <condition_variable>
 #include <cstring>
-#include <functional>
 #include <map>
 #include <memory>
-#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -50,90 +46,12 @@ constexpr size_t kAlign = 256;
 // but with p99 outliers above 1 ms at 10k-20k req/s; 16 MiB / 8x kept.
 constexpr size_t kDefaultMeta = (size_t)16 << 20;
 constexpr size_t kBacklogBatches = 8;   // admission size under a backlog, in max_batch
-// Admissions of at least this many requests build their descriptors on
-// kBuildThreads more host threads (at a saturating load the serving thread
-// spent most of its time there).
-constexpr size_t kParallelRequests = 64;
-constexpr unsigned kBuildThreads = 6;
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 double now_s() {
   using C = std::chrono::steady_clock;
   return std::chrono::duration<double>(C::now().time_since_epoch()).count();
 }
-
-// Host threads that build a large admission's descriptors together with the
-// serving thread: run(count, f) calls f(begin, end) on disjoint chunks of
-// [0, count) and returns when all are done. The workers sleep between calls.
-class Workers {
- public:
-  explicit Workers(unsigned n) {
-    try {
-      for (unsigned i = 0; i < n; i++) threads_.emplace_back([this] { loop(); });
-    } catch (...) {                                   // fewer threads (or none): run() still works
-    }
-  }
-  ~Workers() {
-    {
-      std::lock_guard<std::mutex> g(mu_);
-      stop_ = true;
-      gen_++;
-    }
-    cv_.notify_all();
-    for (std::thread& t : threads_) t.join();
-  }
-  void run(size_t count, const std::function<void(size_t, size_t)>& f) {
-    if (threads_.empty() || count < 2) {
-      if (count) f(0, count);
-      return;
-    }
-    {
-      std::lock_guard<std::mutex> g(mu_);
-      job_ = &f;
-      total_ = count;
-      chunk_ = std::max<size_t>(1, count / (4 * (threads_.size() + 1)));
-      next_.store(0);
-      pending_ = threads_.size();
-      gen_++;
-    }
-    cv_.notify_all();
-    work();
-    std::unique_lock<std::mutex> g(mu_);
-    done_.wait(g, [this] { return pending_ == 0; });
-    job_ = nullptr;
-  }
-
- private:
-  void work() {
-    for (;;) {
-      const size_t b = next_.fetch_add(chunk_);
-      if (b >= total_) return;
-      (*job_)(b, std::min(b + chunk_, total_));
-    }
-  }
-  void loop() {
-    uint64_t seen = 0;
-    for (;;) {
-      {
-        std::unique_lock<std::mutex> g(mu_);
-        cv_.wait(g, [&] { return gen_ != seen; });
-        seen = gen_;
-        if (stop_) return;
-      }
-      work();
-      std::lock_guard<std::mutex> g(mu_);
-      if (--pending_ == 0) done_.notify_one();
-    }
-  }
-  std::vector<std::thread> threads_;
-  std::mutex mu_;
-  std::condition_variable cv_, done_;
-  const std::function<void(size_t, size_t)>* job_ = nullptr;
-  size_t total_ = 0, chunk_ = 1, pending_ = 0;
-  std::atomic<size_t> next_{0};
-  uint64_t gen_ = 0;
-  bool stop_ = false;
-};
 
 // Bytes of the resident descriptor set: every entry of every pool stream and
 // its final-state entry.
@@ -355,8 +273,6 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   std::vector<uint32_t> item_kind;
   std::vector<std::vector<uint32_t>> keeps;     // per admitted request: its kept regular entries
   std::vector<size_t> ent_first;                // per admitted request: its first descriptor
-  // large admissions (a backlog) build their descriptors on a few more host threads
-  Workers workers(per_request ? 0u : std::min(kBuildThreads, std::max(1u, std::thread::hardware_concurrency()) - 1));
   int status = RECOIL_OK;
 
   while (done < n_req && e == cudaSuccess && status == RECOIL_OK) {
@@ -458,24 +374,20 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
         ent_first.resize(n + 1);
         // each request's kept entries (combine, Sec. 3.3, without building a
         // combined stream: the picks index the pool stream's descriptors)
-        const std::function<void(size_t, size_t)> pick = [&](size_t b, size_t end) {
-          for (size_t k = b; k < end; k++) {
-            const recoil_stream* src = pool[req_stream[sl.reqs[k]]];
-            uint32_t target = (uint32_t)src->entries.size() + 1;
-            if (!per_request) {
-              // the request's share of the free warps, but splits no longer than
-              // max_split: a split is one warp's sequential work
-              const double share = syms_batch ? (double)src->n_syms / (double)syms_batch : 1.0;
-              uint64_t want = (uint64_t)std::max(1.0, std::floor(free_w * share));
-              want = std::max<uint64_t>(want, (src->n_syms + max_split - 1) / max_split);
-              want = (want + warps - 1) / warps * warps;
-              target = (uint32_t)std::min<uint64_t>(target, want);
-            }
-            combine_picks(*src, target, keeps[k]);
+        for (size_t k = 0; k < n; k++) {
+          const recoil_stream* src = pool[req_stream[sl.reqs[k]]];
+          uint32_t target = (uint32_t)src->entries.size() + 1;
+          if (!per_request) {
+            // the request's share of the free warps, but splits no longer than
+            // max_split: a split is one warp's sequential work
+            const double share = syms_batch ? (double)src->n_syms / (double)syms_batch : 1.0;
+            uint64_t want = (uint64_t)std::max(1.0, std::floor(free_w * share));
+            want = std::max<uint64_t>(want, (src->n_syms + max_split - 1) / max_split);
+            want = (want + warps - 1) / warps * warps;
+            target = (uint32_t)std::min<uint64_t>(target, want);
           }
-        };
-        if (n >= kParallelRequests) workers.run(n, pick);
-        else pick(0, n);
+          combine_picks(*src, target, keeps[k]);
+        }
         items.clear();
         item_kind.clear();
         uint32_t warps_launch = 0;
@@ -535,21 +447,17 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
         // a reference per kept split into the staging area, each owning from
         // the previous kept split's end
         EntryRef* hr = reinterpret_cast<EntryRef*>(h + off_refs);
-        const std::function<void(size_t, size_t)> copy = [&](size_t b, size_t end) {
-          for (size_t k = b; k < end; k++) {
-            const uint64_t base = pool_first[req_stream[sl.reqs[k]]];
-            const uint64_t last = pool_first[req_stream[sl.reqs[k]] + 1] - 1;   // the final-state entry
-            EntryRef* d = hr + ent_first[k];
-            uint32_t prev_end = 0;
-            for (uint32_t pk : keeps[k]) {
-              *d++ = EntryRef{(uint32_t)(base + pk), prev_end, (uint32_t)k, 0};
-              prev_end = pool_hi1[base + pk];
-            }
-            *d = EntryRef{(uint32_t)last, prev_end, (uint32_t)k, 0};
+        for (size_t k = 0; k < n; k++) {
+          const uint64_t base = pool_first[req_stream[sl.reqs[k]]];
+          const uint64_t last = pool_first[req_stream[sl.reqs[k]] + 1] - 1;   // the final-state entry
+          EntryRef* d = hr + ent_first[k];
+          uint32_t prev_end = 0;
+          for (uint32_t pk : keeps[k]) {
+            *d++ = EntryRef{(uint32_t)(base + pk), prev_end, (uint32_t)k, 0};
+            prev_end = pool_hi1[base + pk];
           }
-        };
-        if (n >= kParallelRequests) workers.run(n, copy);
-        else copy(0, n);
+          *d = EntryRef{(uint32_t)last, prev_end, (uint32_t)k, 0};
+        }
         e = cudaMemcpyAsync(sl.dev, h, meta_bytes, cudaMemcpyHostToDevice, sl.stream);
         if (e == cudaSuccess)
           e = launch_expand_entries(pool_dev, reinterpret_cast<const EntryRef*>(sl.dev + off_refs),
