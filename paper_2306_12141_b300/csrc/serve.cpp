@@ -273,6 +273,8 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
   std::vector<uint32_t> item_kind;
   std::vector<std::vector<uint32_t>> keeps;     // per admitted request: its kept regular entries
   std::vector<size_t> ent_first;                // per admitted request: its first descriptor
+  std::vector<uint32_t> memo_target(pool_count, 0);                 // per pool stream: its last combine
+  std::vector<std::vector<uint32_t>> memo_keep(pool_count);
   int status = RECOIL_OK;
 
   while (done < n_req && e == cudaSuccess && status == RECOIL_OK) {
@@ -386,7 +388,14 @@ int recoil_serve(const recoil_stream* const* pool, uint32_t pool_count, const ui
             want = (want + warps - 1) / warps * warps;
             target = (uint32_t)std::min<uint64_t>(target, want);
           }
-          combine_picks(*src, target, keeps[k]);
+          // the same pool stream combined to the same count again (common
+          // under a backlog, where most requests get one CTA's splits): reuse
+          const uint32_t sid = req_stream[sl.reqs[k]];
+          if (memo_target[sid] != target) {
+            combine_picks(*src, target, memo_keep[sid]);
+            memo_target[sid] = target;
+          }
+          keeps[k] = memo_keep[sid];
         }
         items.clear();
         item_kind.clear();
