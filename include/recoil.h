@@ -434,8 +434,9 @@ int recoil_serve_arena_size(const recoil_stream* const* pool, uint32_t pool_coun
 /*
  * Serve decode requests with continuous batching on the current GPU (the
  * content-delivery setting of Sec. 3.3: each request is combined to the
- * parallelism the decoder has when it is admitted). The pool's words and
- * tables are uploaded once into d_arena (resident). Request r asks for pool
+ * parallelism the decoder has when it is admitted). The pool's words,
+ * tables and split descriptors are uploaded once into d_arena (resident);
+ * an admission sends 16 bytes per kept split. Request r asks for pool
  * stream req_stream[r] at req_arrival_s[r] (seconds from the start, non-
  * decreasing) and is replayed in real time. Arrived requests are admitted in
  * order while the budget and a launch slot allow, combined to their share of
