@@ -243,7 +243,8 @@ __device__ __forceinline__ int ld_keep(const int* p) {
 // ------------------------------------------------------------- word ring
 // Word w of the stream sits at ring[(w mod 512)] and ring[(w mod 512) + 512];
 // with rp = (p mod 512) + 512, word p - k (0 <= k < 32) is ring[rp - k] for
-// any p, and rp may drift down by up to 128 between normalisations.
+// any p, and rp drifts down by at most 256 between normalisations (8 steps
+// of at most 32 words), so reads stay inside the ring.
 
 __device__ __forceinline__ uint4 load_chunk(const uint16_t* __restrict__ words, int chunk, int lane) {
   if (chunk < 0) return make_uint4(0, 0, 0, 0);
