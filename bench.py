@@ -192,11 +192,15 @@ def issue_rate(key: str, mean_ms: float, dev, clocks: dict):
             "instructions_per_launch": inst, "peak_from": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (sampled)"}
 
 
-def kernel_of(info: dict) -> tuple[str, str]:
-    """(symbol dtype, decode kernel) of a static-model stream, as the plan picks its tables."""
-    if info["sym_bytes"] == 2:
-        return "u16", "decode_kernel<kGeneric16>"
-    return "u8", "decode_kernel<kPacked8>" if info["n_bits"] <= 12 else "decode_kernel<kGeneric8>"
+KERNEL_NAMES = ("kPacked8", "kGeneric8", "kGeneric16", "kAdaptive8", "kAdaptive16", "kAdaptive16Wide",
+                "kAdaptive8Pair", "kAdaptive16Pair", "kPacked16")
+
+
+def kernel_of(plan) -> tuple[str, str]:
+    """(symbol dtype, decode kernels) of a plan, from the table kinds it launches."""
+    dtype = "u16" if plan.streams[0].info["sym_bytes"] == 2 else "u8"
+    names = [n for k, n in enumerate(KERNEL_NAMES) if plan.kernels >> k & 1]
+    return dtype, " + ".join(f"decode_kernel<{n}>" for n in names)
 
 
 NOMINAL_HBM_GBS = 8000.0      # HBM3e nominal (~8 TB/s), a second denominator beside the measured copy
@@ -967,7 +971,7 @@ def run_ours(a):
     tkey = (f"batch w{opts['warps_per_cta']} s{split_symbols} l{lanes}" if batch
             else f"{a.dist} w{opts['warps_per_cta']} k{a.splits} l{lanes}")
     traffic = recorded_traffic(tkey) if a.scale == 1.0 and a.streams == workloads.BATCH_STREAMS else None
-    dtype, kernel = kernel_of(plan.streams[0].info)
+    dtype, kernel = kernel_of(plan)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",

@@ -289,12 +289,13 @@ uint32_t recoil_plan_warps_per_cta(const recoil_plan* plan);
 /* Decoder kernels a plan launches, one bit each (host only, no device call). */
 #define RECOIL_KERNEL_PACKED8 1u          /* 8-bit symbols, n <= 12: one packed u32 per slot */
 #define RECOIL_KERNEL_GENERIC8 2u         /* 8-bit symbols otherwise: slot -> symbol, symbol -> (f, F) */
-#define RECOIL_KERNEL_GENERIC16 4u        /* 16-bit symbols, static model */
+#define RECOIL_KERNEL_GENERIC16 4u        /* 16-bit symbols, static model otherwise */
 #define RECOIL_KERNEL_ADAPTIVE8 8u        /* adaptive, 8-bit symbols, one-byte guide entries */
 #define RECOIL_KERNEL_ADAPTIVE16 16u      /* adaptive, 16-bit symbols, alphabet <= 256, one-byte guide entries */
 #define RECOIL_KERNEL_ADAPTIVE16_WIDE 32u /* adaptive, alphabet <= 4096, two-byte guide entries */
 #define RECOIL_KERNEL_ADAPTIVE8_PAIR 64u  /* adaptive, 8-bit symbols, paired layout */
 #define RECOIL_KERNEL_ADAPTIVE16_PAIR 128u /* adaptive, 16-bit symbols, alphabet <= 256, paired layout */
+#define RECOIL_KERNEL_PACKED16 256u       /* 16-bit symbols, n <= 15, every f <= 1023: one packed u32 per slot */
 uint32_t recoil_plan_kernels(const recoil_plan* plan);
 
 void recoil_plan_free(recoil_plan* plan);
@@ -476,7 +477,8 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
  * split count that suits it). Candidates: coder lanes a thread (one, or two
  * with RECOIL_BATCH_TWO_LANES) times the warps_per_cta built for that and for
  * every kind in the batch (one lane: 4, 8, 16, and 32 when a stream is
- * adaptive; two lanes: 4, 8, 16 static, 8, 16, 24 adaptive) times
+ * adaptive or has 16-bit symbols; two lanes: 4, 8, 16 static, 8, 16, 24
+ * adaptive) times
  * split_symbols in {32 Ki, 64 Ki, 128 Ki, 256 Ki} (with
  * RECOIL_TUNE_KEEP_SPLITS: split_symbols 0, the streams as given, for a
  * decoder whose split count is already chosen), and, when an adaptive model

@@ -21,7 +21,7 @@ W = 32
 OK, EINVAL, ECORRUPT, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 BATCH_PER_STREAM, BATCH_NO_SORT, BATCH_GRAPH, BATCH_NO_PAIRS, BATCH_TWO_LANES = 1, 2, 4, 8, 16
 (KERNEL_PACKED8, KERNEL_GENERIC8, KERNEL_GENERIC16, KERNEL_ADAPTIVE8, KERNEL_ADAPTIVE16, KERNEL_ADAPTIVE16_WIDE,
- KERNEL_ADAPTIVE8_PAIR, KERNEL_ADAPTIVE16_PAIR) = (1 << k for k in range(8))
+ KERNEL_ADAPTIVE8_PAIR, KERNEL_ADAPTIVE16_PAIR, KERNEL_PACKED16) = (1 << k for k in range(9))
 
 
 class RecoilError(RuntimeError):

@@ -73,6 +73,20 @@ struct Tables<kPacked8> {
   }
 };
 
+// bias | f << 10 | sym << 20  (16-bit symbols below 2^12, bias = slot - F < f < 2^10)
+template <>
+struct Tables<kPacked16> {
+  const uint32_t* lut;
+  __device__ __forceinline__ void bind(const unsigned char* smem, const DevStream&) {
+    lut = reinterpret_cast<const uint32_t*>(smem);
+  }
+  __device__ __forceinline__ uint32_t step(uint32_t& x, uint32_t n, uint32_t mask) const {
+    const uint32_t e = lut[x & mask];
+    x = ((e >> 10) & 0x3ffu) * (x >> n) + (e & 0x3ffu);
+    return e >> 20;
+  }
+};
+
 // u16 slot -> symbol, then u32 symbol -> (f - 1) << 16 | F
 template <uint32_t KIND>
 struct Tables {
@@ -213,6 +227,10 @@ struct SymOut<kAdaptive16Wide> {
 };
 template <>
 struct SymOut<kAdaptive16Pair> {
+  using T = uint16_t;
+};
+template <>
+struct SymOut<kPacked16> {
   using T = uint16_t;
 };
 
@@ -928,6 +946,7 @@ cudaError_t launch_decode(uint32_t kind, const LaunchArgs& a, unsigned grid, cud
     case kAdaptive16Wide: return launch_k<kAdaptive16Wide>(a, grid, s);
     case kAdaptive8Pair: return launch_k<kAdaptive8Pair>(a, grid, s);
     case kAdaptive16Pair: return launch_k<kAdaptive16Pair>(a, grid, s);
+    case kPacked16: return launch_k<kPacked16>(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -942,6 +961,7 @@ int occupancy_ctas_per_sm(uint32_t kind, uint32_t warps, uint32_t lanes, bool st
     case kAdaptive16Wide: return occupancy_k<kAdaptive16Wide>(warps, lanes, staged, table_smem, out);
     case kAdaptive8Pair: return occupancy_k<kAdaptive8Pair>(warps, lanes, staged, table_smem, out);
     case kAdaptive16Pair: return occupancy_k<kAdaptive16Pair>(warps, lanes, staged, table_smem, out);
+    case kPacked16: return occupancy_k<kPacked16>(warps, lanes, staged, table_smem, out);
   }
   return -1;
 }

@@ -31,13 +31,15 @@ enum TableKind : uint32_t {
   kAdaptive8 = 3,       // 8-bit symbols; one-byte guide entries
   kAdaptive16 = 4,      // 16-bit symbols, alphabet <= 256; one-byte guide entries
   kAdaptive16Wide = 5,  // 16-bit symbols, alphabet <= 4096; two-byte guide entries
-  // the same models as kAdaptive8 / kAdaptive16 in the paired layout: one u32
-  // per symbol holding H(s) and H(s+1), one u16 per guide bucket holding both
-  // bracketing symbols, so a symbol costs two shared reads when the bucket
-  // decides it (a plan stages it where it keeps as many splits resident)
+  // the same models as kAdaptive8 / kAdaptive16 in the paired layout: a block
+  // per PDF of one u32 F(s) | H(s+1) << 16 per symbol and a byte guide over
+  // 2^10 buckets (a plan stages it where it keeps as many splits resident)
   kAdaptive8Pair = 6,
   kAdaptive16Pair = 7,
-  kKinds = 8,
+  // 16-bit symbols, alphabet <= 4096, n <= 15, every f <= 1023: one u32 per
+  // slot = bias | f << 10 | sym << 20 (one shared read a symbol)
+  kPacked16 = 8,
+  kKinds = 9,
 };
 
 static_assert(RECOIL_KERNEL_PACKED8 == 1u << kPacked8 && RECOIL_KERNEL_GENERIC8 == 1u << kGeneric8 &&
@@ -45,10 +47,10 @@ static_assert(RECOIL_KERNEL_PACKED8 == 1u << kPacked8 && RECOIL_KERNEL_GENERIC8 
                   RECOIL_KERNEL_ADAPTIVE16 == 1u << kAdaptive16 &&
                   RECOIL_KERNEL_ADAPTIVE16_WIDE == 1u << kAdaptive16Wide &&
                   RECOIL_KERNEL_ADAPTIVE8_PAIR == 1u << kAdaptive8Pair &&
-                  RECOIL_KERNEL_ADAPTIVE16_PAIR == 1u << kAdaptive16Pair,
+                  RECOIL_KERNEL_ADAPTIVE16_PAIR == 1u << kAdaptive16Pair && RECOIL_KERNEL_PACKED16 == 1u << kPacked16,
               "kernel bits follow the table kinds");
 
-__host__ __device__ constexpr bool is_adaptive_kind(uint32_t k) { return k >= kAdaptive8 && k < kKinds; }
+__host__ __device__ constexpr bool is_adaptive_kind(uint32_t k) { return k >= kAdaptive8 && k <= kAdaptive16Pair; }
 __host__ __device__ constexpr bool is_pair_kind(uint32_t k) { return k == kAdaptive8Pair || k == kAdaptive16Pair; }
 // The paired kind of an adaptive kind with one-byte guide entries (itself otherwise).
 __host__ __device__ constexpr uint32_t pair_kind_of(uint32_t k) {
@@ -119,13 +121,13 @@ struct alignas(16) DevItem {
 };
 
 struct alignas(16) DevControl {
-  uint32_t head[8];          // persistent queue position, one per table kind
+  uint32_t head[16];         // persistent queue position, one per table kind
   uint32_t errors;           // kErr* bits
   uint32_t bad_entry;        // an entry that raised an error (+1), 0 if none
-  uint32_t pad[54];
+  uint32_t pad[46];
 };
 static_assert(sizeof(DevControl) == 256, "DevControl layout");
-static_assert(kKinds <= 8, "one queue head per table kind");
+static_assert(kKinds <= 16, "one queue head per table kind");
 
 // Error flags raised by kernels.
 constexpr uint32_t kErrCorrupt = 1u;         // a state differs from the previous entry's record, or the

@@ -21,12 +21,21 @@ constexpr uint32_t kMaxSmem = 227 * 1024;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// A static 16-bit model whose every slot packs into a u32 (kPacked16):
+// symbols below 2^12, n <= 15 (a LUT of at most 128 KB) and every f <= 1023.
+bool packed16_fits(const Stream& s) {
+  if (s.n_bits > 15 || s.alphabet() > 4096) return false;
+  for (uint32_t f : s.freq)
+    if (f > 1023) return false;
+  return true;
+}
+
 uint32_t table_kind_of(const Stream& s) {
   if (s.adaptive()) {
     if (s.sym_bytes == 1) return kAdaptive8;
     return s.alphabet() <= 256 ? kAdaptive16 : kAdaptive16Wide;
   }
-  if (s.sym_bytes == 2) return kGeneric16;
+  if (s.sym_bytes == 2) return packed16_fits(s) ? kPacked16 : kGeneric16;
   if (s.n_bits <= 12 && !s.constant()) return kPacked8;
   return kGeneric8;
 }
@@ -167,6 +176,15 @@ const std::vector<uint8_t>& table_image(const Stream& s, uint32_t* kind, uint32_
       for (uint32_t sym = 0; sym < A; sym++) {
         const uint32_t f = s.freq[sym];
         for (uint32_t b = 0; b < f; b++) lut[F + b] = b | (sym << 12) | (f << 20);
+        F += f;
+      }
+    } else if (k == kPacked16) {
+      s.table_img.assign(align_up((size_t)slots * 4, 16), 0);
+      uint32_t* lut = reinterpret_cast<uint32_t*>(s.table_img.data());
+      uint32_t F = 0;
+      for (uint32_t sym = 0; sym < A; sym++) {
+        const uint32_t f = s.freq[sym];
+        for (uint32_t b = 0; b < f; b++) lut[F + b] = b | (f << 10) | (sym << 20);
         F += f;
       }
     } else {
@@ -632,9 +650,11 @@ static int device_sms() {
 // 2368 and more within 1% of the best size. Adaptive streams with 64 or more
 // splits an SM take 32-warp CTAs, one per SM, which leaves room for the finer
 // guide (adaptive latents at 9472 splits: 1000 against 945 GB/s).
-static uint32_t auto_warps(uint64_t splits, bool adaptive, uint32_t lanes) {
+static uint32_t auto_warps(uint64_t splits, bool adaptive, bool big_lut, uint32_t lanes) {
   const uint64_t per_sm = splits / lanes / (uint64_t)device_sms();   // warps' worth of splits an SM
   if (adaptive && per_sm >= 64 / lanes) return lanes == 2 ? 24 : 32;
+  // a 128 KB packed 16-bit LUT leaves room for one CTA an SM: make it 32 warps
+  if (big_lut && lanes == 1 && per_sm >= 32) return 32;
   uint32_t w = adaptive && lanes == 2 ? 8 : 4;
   while (w < 16 && (uint64_t)w * 2 <= per_sm) w *= 2;
   return w;
@@ -777,15 +797,16 @@ int recoil_plan_create(const recoil_stream* const* streams, uint32_t count, cons
     P->lanes = (P->opts.flags & RECOIL_BATCH_TWO_LANES) ? 2 : 1;
     if (!P->warps) {
       uint64_t splits = 0;
-      bool adaptive = count > 0;
+      bool adaptive = count > 0, big_lut = false;
       for (uint32_t i = 0; i < count; i++) {
         if (!streams[i]) return fail(RECOIL_EINVAL, "null stream");
         splits += P->opts.split_symbols
                       ? std::max<uint64_t>(1, (streams[i]->n_syms + P->opts.split_symbols - 1) / P->opts.split_symbols)
                       : streams[i]->entries.size() + 1;
         adaptive = adaptive && streams[i]->adaptive();
+        big_lut = big_lut || (table_kind_of(*streams[i]) == kPacked16 && streams[i]->n_bits >= 15);
       }
-      P->warps = auto_warps(splits, adaptive, P->lanes);
+      P->warps = auto_warps(splits, adaptive, big_lut, P->lanes);
     }
     if (!shape_warps_ok(P->warps, P->lanes))
       return fail(RECOIL_EINVAL, P->lanes == 2 ? "two lanes a thread: warps_per_cta must be 4, 8, 16 or 24"
@@ -976,7 +997,8 @@ int recoil_plan_create_shard(const recoil_stream* s, uint32_t world, uint32_t ra
     if (opts) P->opts = *opts;
     P->lanes = (P->opts.flags & RECOIL_BATCH_TWO_LANES) ? 2 : 1;
     P->warps = P->opts.warps_per_cta ? P->opts.warps_per_cta
-                                     : auto_warps(std::max(first, last) - first, s->adaptive(), P->lanes);
+                                     : auto_warps(std::max(first, last) - first, s->adaptive(),
+                                                  table_kind_of(*s) == kPacked16 && s->n_bits >= 15, P->lanes);
     if (!shape_warps_ok(P->warps, P->lanes))
       return fail(RECOIL_EINVAL, P->lanes == 2 ? "two lanes a thread: warps_per_cta must be 4, 8, 16 or 24"
                                                : "warps_per_cta must be 1, 2, 4, 8, 16 or 32");

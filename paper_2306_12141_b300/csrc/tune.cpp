@@ -29,9 +29,11 @@ const uint32_t kSplit[] = {32768, 65536, 131072, 262144};
 // Candidate options: lanes a thread (1 or 2) x warps x split sizes, or lanes
 // x warps alone on the streams' own splits, every shape a kernel is built for
 // with each kind in the batch, and both table layouts where an adaptive
-// model has the paired one. 32-warp CTAs only for adaptive streams (one CTA
-// an SM leaves room for the finer guide); static kinds keep 4 to 16.
-std::vector<recoil_batch_opts> candidates(bool keep_splits, bool has_static, bool has_adaptive, bool pairable) {
+// model has the paired one. 32-warp CTAs only where a large table leaves
+// room for one CTA an SM (adaptive models, 16-bit static models); 8-bit
+// static kinds keep 4 to 16.
+std::vector<recoil_batch_opts> candidates(bool keep_splits, bool has_static, bool has_adaptive, bool pairable,
+                                          bool wide_static) {
   std::vector<recoil_batch_opts> c;
   for (uint32_t layout : {0u, RECOIL_BATCH_NO_PAIRS}) {
     if (layout && !pairable) continue;
@@ -39,7 +41,7 @@ std::vector<recoil_batch_opts> candidates(bool keep_splits, bool has_static, boo
       for (uint32_t w : kWarps) {
         if (has_static && !shape_supported(false, w, lanes)) continue;
         if (has_adaptive && !shape_supported(true, w, lanes)) continue;
-        if (lanes == 1 && w == 32 && !has_adaptive) continue;
+        if (lanes == 1 && w == 32 && !has_adaptive && !wide_static) continue;
         const uint32_t flags = (lanes == 2 ? RECOIL_BATCH_TWO_LANES : 0) | layout;
         if (keep_splits) {
           c.push_back(recoil_batch_opts{w, 0, 0, flags});
@@ -128,6 +130,13 @@ bool any_static(const recoil_stream* const* s, uint32_t count) {
   return false;
 }
 
+// A static model over 16-bit symbols (its tables may fill most of an SM's shared memory).
+bool any_static16(const recoil_stream* const* s, uint32_t count) {
+  for (uint32_t i = 0; i < count; i++)
+    if (s && s[i] && !s[i]->adaptive() && s[i]->sym_bytes == 2) return true;
+  return false;
+}
+
 // An adaptive model with the paired layout (one-byte guide entries: up to 256 symbols).
 bool any_pairable(const recoil_stream* const* s, uint32_t count) {
   for (uint32_t i = 0; i < count; i++)
@@ -148,7 +157,8 @@ int recoil_autotune_workspace_size(const recoil_stream* const* streams, uint32_t
   size_t mx = 0;
   for (bool keep : {false, true})
     for (recoil_batch_opts o :
-         candidates(keep, any_static(streams, count), any_adaptive(streams, count), any_pairable(streams, count))) {
+         candidates(keep, any_static(streams, count), any_adaptive(streams, count), any_pairable(streams, count),
+                    any_static16(streams, count))) {
       size_t b = 0;
       int rc = recoil_workspace_size(streams, count, &o, &b);
       if (rc) return rc;
@@ -182,7 +192,8 @@ int recoil_autotune(const recoil_stream* const* streams, uint32_t count, void* c
   };
   size_t bulk = 0;
   for (const recoil_batch_opts& o :
-       candidates(keep, any_static(streams, count), any_adaptive(streams, count), any_pairable(streams, count))) {
+       candidates(keep, any_static(streams, count), any_adaptive(streams, count), any_pairable(streams, count),
+                    any_static16(streams, count))) {
     Candidate c;
     c.opts = o;
     int rc = recoil_plan_create(streams, count, &c.opts, &c.plan);

@@ -322,7 +322,8 @@ def test_autotune_chooses_a_working_configuration(recoil_lib, tmp_path):
     cs = torch.cuda.current_stream()
     cache = str(tmp_path / "tune.txt")
     best, ms = R.autotune(streams, ptrs, ws, need, cs, steps=2, cache_path=cache)
-    assert best["warps_per_cta"] in (4, 8, 16) and best["split_symbols"] in (32768, 65536, 131072, 262144)
+    # 32-warp CTAs are candidates here: the batch holds 16-bit static models
+    assert best["warps_per_cta"] in (4, 8, 16, 32) and best["split_symbols"] in (32768, 65536, 131072, 262144)
     assert ms > 0
     for s, o in zip(syms, outs):                               # the tuning decodes are exact too
         assert np.array_equal(o.cpu().numpy()[: len(s) * s.itemsize].view(s.dtype), s)
@@ -333,7 +334,7 @@ def test_autotune_chooses_a_working_configuration(recoil_lib, tmp_path):
         assert np.array_equal(out, s)
     # CTA size only, on the streams' own split counts (cached under its own key)
     keep, ms3 = R.autotune(streams, ptrs, ws, need, cs, steps=2, cache_path=cache, keep_splits=True)
-    assert keep["warps_per_cta"] in (4, 8, 16) and keep["split_symbols"] == 0 and ms3 > 0
+    assert keep["warps_per_cta"] in (4, 8, 16, 32) and keep["split_symbols"] == 0 and ms3 > 0
     for s, out in zip(syms, gpu_decode(R, streams, keep)):
         assert np.array_equal(out, s)
     # cache lines carry the lanes a thread and the table layout: key, warps, split symbols, lanes,
