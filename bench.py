@@ -482,6 +482,9 @@ def run_adaptive(a):
     warps = a.warps                                    # 0: the library picks the CTA size
     lane_flag = R.BATCH_TWO_LANES if a.lanes == 2 else 0
     layout_flag = 0                                    # the paired layout where the model has one
+
+    def layout_name(flag):
+        return "two-byte guide" if a.alphabet > 256 else ("one-byte guide" if flag else "paired")
     cs = torch.cuda.Stream(device=dev)
     out = torch.empty(len(s) * 2, dtype=torch.uint8, device=dev)
     ref = torch.from_numpy(s.view(np.uint8)).to(dev)
@@ -519,7 +522,7 @@ def run_adaptive(a):
             lane_flag = best["flags"] & R.BATCH_TWO_LANES
             layout_flag = best["flags"] & R.BATCH_NO_PAIRS
             tuned = {"warps_per_cta": warps, "lanes_per_thread": 2 if lane_flag else 1,
-                     "table_layout": "byte guide" if layout_flag else "paired", "ms": round(tms, 4)}
+                     "table_layout": layout_name(layout_flag), "ms": round(tms, 4)}
             del tws
         plan = R.Plan([c], {"warps_per_cta": warps, "flags": R.BATCH_GRAPH | lane_flag | layout_flag})
         warps = plan.warps_per_cta
@@ -567,7 +570,7 @@ def run_adaptive(a):
                                    f"Gaussian scale tables (0.11..256) over {a.alphabet} values, n=16, W=32",
                        "splits": c.info["n_entries"], "warps_per_cta": warps,
                        "lanes_per_thread": 2 if lane_flag else 1, "autotuned": tuned,
-                       "table_layout": "byte guide" if layout_flag or a.alphabet > 256 else "paired",
+                       "table_layout": layout_name(layout_flag),
                        "symbols_bytes": out_bytes,
                        "compressed_bytes": 2 * c.info["n_words"] + 4 * 32, "table_number_bytes": len(s),
                        "l2": "inputs larger than L2 (no flush)", "scale": a.scale},
