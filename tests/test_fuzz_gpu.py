@@ -1,0 +1,60 @@
+"""Randomised GPU parity: streams drawn at random (alphabet, n, length, skew, symbol width), encoded
+by the library, combined to a random split count and decoded on the GPU with a random CTA shape,
+alone and all together in one batch; every output is the input and the oracle's split decode."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _draw(k):
+    g = np.random.default_rng(1000 + k)
+    n = int(g.integers(1, 17))
+    sym_bytes = int(g.integers(1, 3))
+    A = int(g.integers(1, min(1 << n, 256 if sym_bytes == 1 else 4096) + 1))
+    N = int(g.choice([int(g.integers(1, 100)), int(g.integers(100, 200_000))]))
+    p = g.random(A) ** (1.0 + 12.0 * g.random())
+    p /= p.sum()
+    s = g.choice(A, size=N, p=p).astype(np.uint8 if sym_bytes == 1 else np.uint16)
+    return s, n, int(g.integers(1, 400)), int(g.integers(1, 500)), int(g.choice([1, 2, 4, 8, 16, 32]))
+
+
+def _decode(R, streams, warps):
+    plan = R.Plan(streams, {"warps_per_cta": warps})
+    ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device="cuda")
+    outs = [torch.full((max(1, st.info["n_syms"] * st.info["sym_bytes"]),), 0xAB, dtype=torch.uint8, device="cuda")
+            for st in streams]
+    plan.upload(ws)
+    plan.decode([o.data_ptr() for o in outs])
+    assert plan.errors() == 0, R.recoil_last_error()
+    res = []
+    for o, st in zip(outs, streams):
+        a = o.cpu().numpy()[: st.info["n_syms"] * st.info["sym_bytes"]]
+        res.append(a.view(np.uint16) if st.info["sym_bytes"] == 2 else a)
+    return res
+
+
+CASES = [_draw(k) for k in range(40)]
+
+
+@pytest.mark.parametrize("k", range(len(CASES)))
+def test_random_stream_decodes_exactly(recoil_lib, k):
+    R = recoil_lib
+    s, n, M, target, warps = CASES[k]
+    c = R.combine_splits(R.encode_with_splits(s, n, M), target)
+    (got,) = _decode(R, [c], warps)
+    assert np.array_equal(got, s)
+    o = oracle.combined(oracle.encode_with_splits(s, n, M, alphabet=None), target)
+    assert np.array_equal(got, oracle.decode_splits(o).astype(s.dtype))
+
+
+def test_random_streams_in_one_batch(recoil_lib):
+    """Every kind of table the draws produce, decoded together (one launch per kind)."""
+    R = recoil_lib
+    streams = [R.combine_splits(R.encode_with_splits(s, n, M), t) for s, n, M, t, _ in CASES]
+    for warps in (4, 16):
+        for got, (s, *_rest) in zip(_decode(R, streams, warps), CASES):
+            assert np.array_equal(got, s)
