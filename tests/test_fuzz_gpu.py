@@ -1,6 +1,7 @@
-"""Randomised GPU parity: streams drawn at random (alphabet, n, length, skew, symbol width), encoded
-by the library, combined to a random split count and decoded on the GPU with a random CTA shape,
-alone and all together in one batch; every output is the input and the oracle's split decode."""
+"""Randomised GPU parity: streams drawn at random (alphabet, n, length, skew, symbol width; static
+models, and adaptive ones with a random PDF row per symbol index), encoded by the library, combined
+to a random split count and decoded on the GPU with a random CTA shape, alone and all together in
+one batch; every output is the input and the oracle's split decode."""
 import numpy as np
 import pytest
 
@@ -58,3 +59,52 @@ def test_random_streams_in_one_batch(recoil_lib):
     for warps in (4, 16):
         for got, (s, *_rest) in zip(_decode(R, streams, warps), CASES):
             assert np.array_equal(got, s)
+
+
+def _quantised_rows(g, T, A, n):
+    """T random PDFs over A symbols, each quantised to frequencies >= 1 summing to 2^n."""
+    rows = np.empty((T, A), dtype=np.uint32)
+    for t in range(T):
+        p = g.random(A) ** (1.0 + 12.0 * g.random())
+        p /= p.sum()
+        f = np.floor(p * ((1 << n) - A)).astype(np.int64) + 1
+        f[np.argmax(f)] += (1 << n) - f.sum()
+        rows[t] = f
+    return rows
+
+
+def _draw_adaptive(k):
+    g = np.random.default_rng(5000 + k)
+    n = int(g.integers(2, 17))
+    sym_bytes = int(g.integers(1, 3))
+    A = int(g.integers(2, min(1 << n, 256 if sym_bytes == 1 else 4096) + 1))
+    T = int(g.integers(1, 9))
+    tables = _quantised_rows(g, T, A, n)
+    N = int(g.choice([int(g.integers(1, 100)), int(g.integers(100, 120_000))]))
+    tid = g.integers(0, T, size=N).astype(np.uint8)
+    cdf = np.cumsum(tables, axis=1) / float(1 << n)
+    u = g.random(N)
+    s = np.array([np.searchsorted(cdf[t], x, side="right") for t, x in zip(tid, u)])
+    s = np.minimum(s, A - 1).astype(np.uint8 if sym_bytes == 1 else np.uint16)
+    return s, n, tables, tid, int(g.integers(1, 300)), int(g.integers(1, 400)), int(g.choice([4, 8, 16, 32]))
+
+
+ADAPTIVE = [_draw_adaptive(k) for k in range(16)]
+
+
+@pytest.mark.parametrize("k", range(len(ADAPTIVE)))
+def test_random_adaptive_stream_decodes_exactly(recoil_lib, k):
+    R = recoil_lib
+    s, n, tables, tid, M, target, warps = ADAPTIVE[k]
+    c = R.combine_splits(R.encode_adaptive(s, n, tables, tid, M), target)
+    for flags in (0, R.BATCH_NO_PAIRS):
+        plan = R.Plan([c], {"warps_per_cta": warps, "flags": flags})
+        ws = torch.empty(max(256, plan.workspace_size), dtype=torch.uint8, device="cuda")
+        out = torch.full((max(1, len(s) * s.itemsize),), 0xAB, dtype=torch.uint8, device="cuda")
+        plan.upload(ws)
+        plan.decode([out.data_ptr()])
+        assert plan.errors() == 0, R.recoil_last_error()
+        got = out.cpu().numpy()[: len(s) * s.itemsize].view(s.dtype)
+        assert np.array_equal(got, s), flags
+    o = oracle.combined(oracle.encode_adaptive_with_splits(s, tid, tables, n, M), target)
+    assert np.array_equal(oracle.decode_splits(o).astype(s.dtype), s)
