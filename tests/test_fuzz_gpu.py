@@ -108,3 +108,38 @@ def test_random_adaptive_stream_decodes_exactly(recoil_lib, k):
         assert np.array_equal(got, s), flags
     o = oracle.combined(oracle.encode_adaptive_with_splits(s, tid, tables, n, M), target)
     assert np.array_equal(oracle.decode_splits(o).astype(s.dtype), s)
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_random_serving_runs(recoil_lib, k):
+    """Serving with a random pool (static models of every table kind, and adaptive ones), random
+    request picks, bursty arrivals, a random CTA size, backlog factor and descriptor area: every
+    request's output is its stream's input, whatever admission carried it."""
+    R = recoil_lib
+    g = np.random.default_rng(9000 + k)
+    members = [CASES[int(i)] for i in g.choice(len(CASES), size=6, replace=False)]
+    pool = [R.encode_with_splits(s, n, max(1, min(M, len(s) // 64 + 1))) for s, n, M, _t, _w in members]
+    syms = [m[0] for m in members]
+    if k % 2:
+        s, n, tables, tid, M, _t, _w = ADAPTIVE[int(g.integers(len(ADAPTIVE)))]
+        pool.append(R.encode_adaptive(s, n, tables, tid, max(1, min(M, len(s) // 64 + 1))))
+        syms.append(s)
+    n_req = int(g.integers(50, 400))
+    picks = g.integers(0, len(pool), size=n_req)
+    gaps = np.where(g.random(n_req) < 0.3, 0.0, g.exponential(1.0 / float(g.choice([2e3, 2e4, 2e5])), size=n_req))
+    arrive = np.cumsum(gaps)
+    outs = [torch.full((max(1, len(syms[p]) * syms[p].itemsize),), 0xAB, dtype=torch.uint8, device="cuda")
+            for p in picks]
+    budget = 1 << 30
+    meta = int(g.choice([0, 1 << 20, 4 << 20]))
+    warps = int(g.choice([4, 8, 16]))
+    need = R.serve_arena_size(pool, budget, meta_bytes=meta, warps_per_cta=warps)
+    arena = torch.empty(need, dtype=torch.uint8, device="cuda")
+    res, stats = R.serve(pool, picks, arrive, arena, need, budget, outs=[o.data_ptr() for o in outs],
+                         warps_per_cta=warps, max_inflight=int(g.integers(1, 6)), max_batch=int(g.integers(1, 40)),
+                         meta_bytes=meta, timeout_s=60.0)
+    assert stats["requests"] == n_req
+    for r, p in enumerate(picks):
+        s = syms[p]
+        got = outs[r].cpu().numpy()[: len(s) * s.itemsize].view(s.dtype)
+        assert np.array_equal(got, s), (k, r, int(p))
